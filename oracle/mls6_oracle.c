@@ -1,0 +1,729 @@
+/*
+ * mls6_oracle.c -- TEST INFRASTRUCTURE ONLY (see mls6_oracle.h).
+ *
+ * A plain FP64 restatement of multilevel summation for r^-6 dispersion,
+ * written step by step in the order and notation of Sec. II.B of
+ * arXiv 1308.4005: anterpolation, restriction, evaluation on every level,
+ * prolongation, interpolation.  Nothing here is blocked, fused or reordered
+ * beyond hoisting the per-offset kernel values out of the grid loops.  Every
+ * parallel loop writes only its own output slot and every sum over slots is
+ * a serial loop, so results do not depend on the thread count.
+ *
+ * Readings of the paper that this file takes (each also listed in the
+ * design notes of the repository):
+ *  R1 basis scale: phi^k uses the level-k spacing 2^(k-1) h (Eq. def-phi
+ *     prints 2^k h; Sec. III.D gives grid k the spacing 2^(k-1) h).
+ *  R2 Eq. (evaluation) applies g_k of Eqs. (g_0), (g_k), (g_l); on levels
+ *     k >= 1 every node pair counts, mu = nu included.
+ *  R3 E = -1/2 xi^T G xi with xi = c; the self term enters as
+ *     +1/2 gamma(0)/a^6 sum c_i^2 (Eq. self-interaction-energy).
+ *  R4 forces are the exact gradient of the MLS energy.
+ *  R6 periodic basis functions and kernels are sums over images, which
+ *     wrapping node indices with repetition reproduces on small grids.
+ *  R7 the coarsest-level table (Eq. last-grid-periodic-transformed) is a
+ *     direct image sum out to a radius R plus the continuum tail beyond R.
+ *  R8 virial: strain derivative with grids deforming with the cell.
+ *  R9 cutoff tests are strict (r < cutoff); g_k is exactly 0 beyond.
+ */
+#include "mls6_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 0;
+
+void orc_set_threads(int n) { g_threads = n; }
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+#define NT orc_get_threads()
+
+/* ------------------------------------------------------------------ */
+/* Closed forms.                                                       */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (gamma): 15/8 - 5/4 rho^12 + 3/8 rho^24 below 1, rho^-6 above. */
+double orc_gamma(double rho) {
+  if (rho < 1.0) {
+    double r12 = pow(rho, 12.0);
+    return 15.0 / 8.0 - 5.0 / 4.0 * r12 + 3.0 / 8.0 * r12 * r12;
+  }
+  return pow(rho, -6.0);
+}
+
+double orc_dgamma(double rho) {
+  if (rho < 1.0) return -15.0 * pow(rho, 11.0) + 9.0 * pow(rho, 23.0);
+  return -6.0 * pow(rho, -7.0);
+}
+
+/* Eqs. (g_0), (g_k), (g_l).  Level k uses the cutoff 2^k a for k < l;
+ * beyond the cutoff the value is exactly 0 (reading R9). */
+double orc_gk(int k, int l, double a, double r) {
+  if (k == 0) {
+    if (r >= a) return 0.0;
+    return pow(r, -6.0) - pow(a, -6.0) * orc_gamma(r / a);
+  }
+  double s_in = ldexp(a, k - 1); /* 2^(k-1) a */
+  if (k == l) return pow(s_in, -6.0) * orc_gamma(r / s_in);
+  double s_out = ldexp(a, k); /* 2^k a */
+  if (r >= s_out) return 0.0;
+  return pow(s_in, -6.0) * orc_gamma(r / s_in) - pow(s_out, -6.0) * orc_gamma(r / s_out);
+}
+
+double orc_dgk(int k, int l, double a, double r) {
+  if (k == 0) {
+    if (r >= a) return 0.0;
+    return -6.0 * pow(r, -7.0) - pow(a, -7.0) * orc_dgamma(r / a);
+  }
+  double s_in = ldexp(a, k - 1);
+  if (k == l) return pow(s_in, -7.0) * orc_dgamma(r / s_in);
+  double s_out = ldexp(a, k);
+  if (r >= s_out) return 0.0;
+  return pow(s_in, -7.0) * orc_dgamma(r / s_in) - pow(s_out, -7.0) * orc_dgamma(r / s_out);
+}
+
+/* Eq. (Phi-Hermite): the cubic nodal basis function with support |t| < 2. */
+double orc_Phi(double t) {
+  double u = fabs(t);
+  if (u <= 1.0) return (1.0 - u) * (1.0 + u - 1.5 * t * t);
+  if (u <= 2.0) return -0.5 * (u - 1.0) * (2.0 - u) * (2.0 - u);
+  return 0.0;
+}
+
+double orc_dPhi(double t) {
+  double u = fabs(t), sg = t < 0.0 ? -1.0 : 1.0;
+  if (u <= 1.0) return sg * (-5.0 * u + 4.5 * u * u);
+  if (u <= 2.0) return sg * (-0.5 * (2.0 - u) * (4.0 - 3.0 * u));
+  return 0.0;
+}
+
+int orc_grid_dims(const double L[3], double h, int levels, int n_out[3]) {
+  if (!(h > 0.0) || levels < 1 || levels > 20) return -1;
+  long m = 1L << (levels - 1);
+  for (int d = 0; d < 3; ++d) {
+    if (!(L[d] > 0.0)) return -1;
+    double u = L[d] / h / (double)m; /* grid points in units of m */
+    long lo = (long)floor(u), hi = lo + 1;
+    long pick = (u - (double)lo < (double)hi - u) ? lo : hi; /* tie -> hi (finer) */
+    if (pick < 1) pick = 1;
+    n_out[d] = (int)(pick * m);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Small linear algebra on the cell.                                   */
+/* ------------------------------------------------------------------ */
+
+static double det3(const double H[9]) {
+  return H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+         H[2] * (H[3] * H[7] - H[4] * H[6]);
+}
+
+static int inv3(const double H[9], double G[9]) {
+  double d = det3(H);
+  if (!(fabs(d) > 0.0)) return -1;
+  G[0] = (H[4] * H[8] - H[5] * H[7]) / d;
+  G[1] = (H[2] * H[7] - H[1] * H[8]) / d;
+  G[2] = (H[1] * H[5] - H[2] * H[4]) / d;
+  G[3] = (H[5] * H[6] - H[3] * H[8]) / d;
+  G[4] = (H[0] * H[8] - H[2] * H[6]) / d;
+  G[5] = (H[2] * H[3] - H[0] * H[5]) / d;
+  G[6] = (H[3] * H[7] - H[4] * H[6]) / d;
+  G[7] = (H[1] * H[6] - H[0] * H[7]) / d;
+  G[8] = (H[0] * H[4] - H[1] * H[3]) / d;
+  return 0;
+}
+
+static void mv3(const double M[9], const double v[3], double o[3]) {
+  for (int r = 0; r < 3; ++r) o[r] = M[3 * r] * v[0] + M[3 * r + 1] * v[1] + M[3 * r + 2] * v[2];
+}
+
+static double rownorm(const double M[9], int r) {
+  return sqrt(M[3 * r] * M[3 * r] + M[3 * r + 1] * M[3 * r + 1] + M[3 * r + 2] * M[3 * r + 2]);
+}
+
+static long wrapi(long i, long n) {
+  long m = i % n;
+  return m < 0 ? m + n : m;
+}
+
+/* Accumulate the symmetric outer product s * (d (x) d) into w[6]. */
+static void add_outer(double w[6], double s, const double d[3]) {
+  w[0] += s * d[0] * d[0];
+  w[1] += s * d[1] * d[1];
+  w[2] += s * d[2] * d[2];
+  w[3] += s * d[0] * d[1];
+  w[4] += s * d[0] * d[2];
+  w[5] += s * d[1] * d[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* Problem context.                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Image radius of the coarsest-level table.  Given r_img > 0 it is used as
+ * is; otherwise 64 times the longest cell vector, reduced for large
+ * coarsest grids so that (points) x (images) stays near 3e7 (successive
+ * doublings of R at 64 L change the table by ~1e-10 relative).  Never below
+ * twice 2^(l-1) a, so that g_l = r^-6 beyond R and the tail is exact in
+ * the continuum limit. */
+static double default_radius(const double H[9], const int nl[3], int levels, double a,
+                             double r_img) {
+  double Lmax = 0.0;
+  for (int col = 0; col < 3; ++col) {
+    double v = sqrt(H[col] * H[col] + H[3 + col] * H[3 + col] + H[6 + col] * H[6 + col]);
+    if (v > Lmax) Lmax = v;
+  }
+  double R = r_img;
+  if (!(R > 0.0)) {
+    double np = (double)nl[0] * nl[1] * nl[2];
+    double f = cbrt(3.0e7 / (4.19 * np));
+    if (f > 64.0) f = 64.0;
+    if (f < 12.0) f = 12.0;
+    R = f * Lmax;
+  }
+  if (R < 2.0 * ldexp(a, levels - 1)) R = 2.0 * ldexp(a, levels - 1);
+  return R;
+}
+
+typedef struct {
+  double H[9], G[9]; /* cell and its inverse */
+  double a, R;       /* local cutoff, coarsest-table image radius */
+  int l;             /* number of grid levels */
+  int n[21][3];      /* n[k] = points per axis on level k (k = 1..l) */
+  long np[21];       /* points on level k */
+  int64_t N;
+  double* s;         /* wrapped fractional positions, N*3 */
+  double* x;         /* wrapped Cartesian positions, N*3 */
+  const double* c;
+  double* q[21];     /* xi^k (Eq. anterpolation / restriction) */
+  double* e[21];     /* e^k (Eq. evaluation) */
+  double* et[21];    /* e^{k,tot} (prolongation) */
+  double w_grid[6];  /* grid virial */
+} ctx_t;
+
+static void ctx_free(ctx_t* C) {
+  free(C->s);
+  free(C->x);
+  for (int k = 1; k <= C->l; ++k) {
+    free(C->q[k]);
+    free(C->e[k]);
+    free(C->et[k]);
+  }
+}
+
+static int ctx_init(ctx_t* C, const double H[9], double a, const int n[3], int levels,
+                    double r_img, int64_t N, const double* x, const double* c) {
+  memset(C, 0, sizeof(*C));
+  if (levels < 1 || levels > 20 || !(a > 0.0) || N < 0) return -1;
+  memcpy(C->H, H, sizeof(C->H));
+  if (inv3(H, C->G)) return -1;
+  C->a = a;
+  C->l = levels;
+  C->N = N;
+  C->c = c;
+  long m = 1L << (levels - 1);
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 1 || n[d] % m) return -2;
+  for (int k = 1; k <= levels; ++k) {
+    long div = 1L << (k - 1);
+    C->np[k] = 1;
+    for (int d = 0; d < 3; ++d) {
+      C->n[k][d] = (int)(n[d] / div);
+      C->np[k] *= C->n[k][d];
+    }
+  }
+  C->R = default_radius(H, C->n[levels], levels, a, r_img);
+  C->s = (double*)malloc(sizeof(double) * 3 * (N > 0 ? N : 1));
+  C->x = (double*)malloc(sizeof(double) * 3 * (N > 0 ? N : 1));
+  for (int k = 1; k <= levels; ++k) {
+    C->q[k] = (double*)calloc((size_t)C->np[k], sizeof(double));
+    C->e[k] = (double*)calloc((size_t)C->np[k], sizeof(double));
+    C->et[k] = (double*)calloc((size_t)C->np[k], sizeof(double));
+  }
+  /* Wrap positions into the cell: fractional s in [0,1). */
+  for (int64_t i = 0; i < N; ++i) {
+    double si[3];
+    mv3(C->G, x + 3 * i, si);
+    for (int d = 0; d < 3; ++d) {
+      si[d] -= floor(si[d]);
+      if (si[d] >= 1.0) si[d] = 0.0;
+      C->s[3 * i + d] = si[d];
+    }
+    mv3(C->H, si, C->x + 3 * i);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Local part, Eq. (g_0): every image pair with r < a.                 */
+/* ------------------------------------------------------------------ */
+
+static void local_atom(const ctx_t* C, int64_t i, double* e0, double F[3], double W[6]) {
+  double A[3];
+  for (int d = 0; d < 3; ++d) A[d] = C->a * rownorm(C->G, d);
+  *e0 = 0.0;
+  F[0] = F[1] = F[2] = 0.0;
+  for (int d = 0; d < 6; ++d) W[d] = 0.0;
+  const double* si = C->s + 3 * i;
+  double ci = C->c[i];
+  for (int64_t j = 0; j < C->N; ++j) {
+    const double* sj = C->s + 3 * j;
+    double ds[3] = {sj[0] - si[0], sj[1] - si[1], sj[2] - si[2]};
+    long lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = (long)ceil(-A[d] - ds[d]);
+      hi[d] = (long)floor(A[d] - ds[d]);
+    }
+    for (long n0 = lo[0]; n0 <= hi[0]; ++n0)
+      for (long n1 = lo[1]; n1 <= hi[1]; ++n1)
+        for (long n2 = lo[2]; n2 <= hi[2]; ++n2) {
+          if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
+          double t[3] = {ds[0] + n0, ds[1] + n1, ds[2] + n2}, d3[3];
+          mv3(C->H, t, d3); /* d = x_j - x_i + H n */
+          double r = sqrt(d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2]);
+          if (!(r < C->a)) continue;
+          double cj = C->c[j];
+          *e0 += cj * orc_gk(0, C->l, C->a, r);
+          double gp = orc_dgk(0, C->l, C->a, r) / r;
+          for (int d = 0; d < 3; ++d) F[d] -= ci * cj * gp * d3[d];
+          add_outer(W, 0.5 * ci * cj * gp, d3);
+        }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid part.                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (anterpolation): xi^1_mu = sum_j phi^1_mu(x_j) xi_j. */
+static void anterpolate(ctx_t* C) {
+  const int* n = C->n[1];
+  for (int64_t j = 0; j < C->N; ++j) {
+    double u[3];
+    for (int d = 0; d < 3; ++d) u[d] = n[d] * C->s[3 * j + d];
+    for (long m0 = (long)ceil(u[0] - 2.0); m0 <= (long)floor(u[0] + 2.0); ++m0)
+      for (long m1 = (long)ceil(u[1] - 2.0); m1 <= (long)floor(u[1] + 2.0); ++m1)
+        for (long m2 = (long)ceil(u[2] - 2.0); m2 <= (long)floor(u[2] + 2.0); ++m2) {
+          double w = orc_Phi(u[0] - m0) * orc_Phi(u[1] - m1) * orc_Phi(u[2] - m2);
+          long idx = wrapi(m0, n[0]) + n[0] * (wrapi(m1, n[1]) + n[1] * wrapi(m2, n[2]));
+          C->q[1][idx] += w * C->c[j];
+        }
+  }
+}
+
+/* Restriction: xi^{k+1}_mu = sum_nu phi^{k+1}_mu(X^k_nu) xi^k_nu.  In units
+ * of the coarse spacing the fine node nu sits at nu/2, so the weight is
+ * prod_d Phi(nu_d/2 - mu_d); the full 3-D box of fine nodes with nonzero
+ * weight is visited (no separable passes). */
+static void restrict_level(ctx_t* C, int k) {
+  const int* nf = C->n[k];
+  const int* nc = C->n[k + 1];
+  const double* qf = C->q[k];
+  double* qc = C->q[k + 1];
+#pragma omp parallel for num_threads(NT) schedule(static)
+  for (long mu = 0; mu < C->np[k + 1]; ++mu) {
+    long m0 = mu % nc[0], m1 = (mu / nc[0]) % nc[1], m2 = mu / ((long)nc[0] * nc[1]);
+    double acc = 0.0;
+    for (long v2 = 2 * m2 - 4; v2 <= 2 * m2 + 4; ++v2)
+      for (long v1 = 2 * m1 - 4; v1 <= 2 * m1 + 4; ++v1)
+        for (long v0 = 2 * m0 - 4; v0 <= 2 * m0 + 4; ++v0) {
+          double w = orc_Phi(0.5 * v0 - m0) * orc_Phi(0.5 * v1 - m1) * orc_Phi(0.5 * v2 - m2);
+          if (w == 0.0) continue;
+          long idx = wrapi(v0, nf[0]) + nf[0] * (wrapi(v1, nf[1]) + nf[1] * wrapi(v2, nf[2]));
+          acc += w * qf[idx];
+        }
+    qc[mu] = acc;
+  }
+}
+
+typedef struct {
+  long m[3];
+  double g;      /* g_k(|r_m|) */
+  double v[6];   /* g_k'(|r_m|)/|r_m| r_m (x) r_m */
+} tap_t;
+
+/* All node offsets m with |H m/n_k| < 2^k a on level k < l, with kernel
+ * values; the list is the cutoff sum of Eq. (evaluation) with its loop over
+ * nu written as nu = mu + m (every image pair inside the cutoff once). */
+static tap_t* level_taps(const ctx_t* C, int k, long* count) {
+  const int* n = C->n[k];
+  double cut = ldexp(C->a, k);
+  long M[3];
+  for (int d = 0; d < 3; ++d) M[d] = (long)ceil(cut * n[d] * rownorm(C->G, d)) + 1;
+  long cap = (2 * M[0] + 1) * (2 * M[1] + 1) * (2 * M[2] + 1), cnt = 0;
+  tap_t* t = (tap_t*)malloc(sizeof(tap_t) * (size_t)cap);
+  for (long m2 = -M[2]; m2 <= M[2]; ++m2)
+    for (long m1 = -M[1]; m1 <= M[1]; ++m1)
+      for (long m0 = -M[0]; m0 <= M[0]; ++m0) {
+        double f[3] = {(double)m0 / n[0], (double)m1 / n[1], (double)m2 / n[2]}, r3[3];
+        mv3(C->H, f, r3);
+        double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+        if (!(r < cut)) continue;
+        tap_t* tp = &t[cnt++];
+        tp->m[0] = m0;
+        tp->m[1] = m1;
+        tp->m[2] = m2;
+        tp->g = orc_gk(k, C->l, C->a, r);
+        for (int d = 0; d < 6; ++d) tp->v[d] = 0.0;
+        if (r > 0.0) add_outer(tp->v, orc_dgk(k, C->l, C->a, r) / r, r3);
+      }
+  *count = cnt;
+  return t;
+}
+
+/* Eq. (evaluation) on a level k < l, plus its strain derivative. */
+static void evaluate_level(ctx_t* C, int k) {
+  long cnt;
+  tap_t* taps = level_taps(C, k, &cnt);
+  const int* n = C->n[k];
+  const double* q = C->q[k];
+  double* e = C->e[k];
+  double* wv = (double*)calloc((size_t)C->np[k] * 6, sizeof(double));
+#pragma omp parallel for num_threads(NT) schedule(static)
+  for (long mu = 0; mu < C->np[k]; ++mu) {
+    long m0 = mu % n[0], m1 = (mu / n[0]) % n[1], m2 = mu / ((long)n[0] * n[1]);
+    double acc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+    for (long t = 0; t < cnt; ++t) {
+      long idx = wrapi(m0 + taps[t].m[0], n[0]) +
+                 n[0] * (wrapi(m1 + taps[t].m[1], n[1]) + n[1] * wrapi(m2 + taps[t].m[2], n[2]));
+      acc += taps[t].g * q[idx];
+      for (int d = 0; d < 6; ++d) v[d] += taps[t].v[d] * q[idx];
+    }
+    e[mu] = acc;
+    for (int d = 0; d < 6; ++d) wv[6 * mu + d] = 0.5 * q[mu] * v[d];
+  }
+  for (long mu = 0; mu < C->np[k]; ++mu)
+    for (int d = 0; d < 6; ++d) C->w_grid[d] += wv[6 * mu + d];
+  free(wv);
+  free(taps);
+}
+
+/* Eq. (last-grid-periodic-transformed): T(m) = sum_{n in Z^3} g_l(|H(m/n_l + n)|),
+ * by direct summation over |.| < R plus the continuum tail: beyond R,
+ * g_l(r) = r^-6 and the lattice sum is replaced by its integral
+ * (1/det H) int_{r>R} r^-6 d^3r = 4 pi / (3 R^3 det H).  The virial table
+ * V(m) = sum_n g_l'(r)/r r (x) r gets the tail -8 pi/(3 R^3 det H) * delta. */
+static void top_tables(const double H[9], const double G[9], double a, const int nl[3],
+                       int l, double R, double* T, double* V) {
+  long np = (long)nl[0] * nl[1] * nl[2];
+  double vol = fabs(det3(H));
+  double tailE = 4.0 * M_PI / (3.0 * R * R * R * vol);
+  double tailV = -8.0 * M_PI / (3.0 * R * R * R * vol);
+  double A[3];
+  for (int d = 0; d < 3; ++d) A[d] = R * rownorm(G, d);
+#pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
+  for (long m = 0; m < np; ++m) {
+    long m0 = m % nl[0], m1 = (m / nl[0]) % nl[1], m2 = m / ((long)nl[0] * nl[1]);
+    double t0[3] = {(double)m0 / nl[0], (double)m1 / nl[1], (double)m2 / nl[2]};
+    long lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = (long)ceil(-A[d] - t0[d]);
+      hi[d] = (long)floor(A[d] - t0[d]);
+    }
+    double acc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+    for (long i0 = lo[0]; i0 <= hi[0]; ++i0)
+      for (long i1 = lo[1]; i1 <= hi[1]; ++i1)
+        for (long i2 = lo[2]; i2 <= hi[2]; ++i2) {
+          double f[3] = {t0[0] + i0, t0[1] + i1, t0[2] + i2}, r3[3];
+          mv3(H, f, r3);
+          double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+          if (!(r < R)) continue;
+          acc += orc_gk(l, l, a, r);
+          if (r > 0.0) add_outer(v, orc_dgk(l, l, a, r) / r, r3);
+        }
+    T[m] = acc + tailE;
+    if (V) {
+      for (int d = 0; d < 6; ++d) V[d * np + m] = v[d] + (d < 3 ? tailV : 0.0);
+    }
+  }
+}
+
+/* Evaluation on the coarsest level l (all-to-all over the periodic grid). */
+static void evaluate_top(ctx_t* C) {
+  int l = C->l;
+  const int* n = C->n[l];
+  long np = C->np[l];
+  double* T = (double*)malloc(sizeof(double) * (size_t)np);
+  double* V = (double*)malloc(sizeof(double) * (size_t)np * 6);
+  top_tables(C->H, C->G, C->a, n, l, C->R, T, V);
+  const double* q = C->q[l];
+  double* wv = (double*)calloc((size_t)np * 6, sizeof(double));
+#pragma omp parallel for num_threads(NT) schedule(static)
+  for (long mu = 0; mu < np; ++mu) {
+    long u0 = mu % n[0], u1 = (mu / n[0]) % n[1], u2 = mu / ((long)n[0] * n[1]);
+    double acc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+    for (long nu = 0; nu < np; ++nu) {
+      long v0 = nu % n[0], v1 = (nu / n[0]) % n[1], v2 = nu / ((long)n[0] * n[1]);
+      long m = wrapi(u0 - v0, n[0]) + n[0] * (wrapi(u1 - v1, n[1]) + n[1] * wrapi(u2 - v2, n[2]));
+      acc += T[m] * q[nu];
+      for (int d = 0; d < 6; ++d) v[d] += V[d * np + m] * q[nu];
+    }
+    C->e[l][mu] = acc;
+    for (int d = 0; d < 6; ++d) wv[6 * mu + d] = 0.5 * q[mu] * v[d];
+  }
+  for (long mu = 0; mu < np; ++mu)
+    for (int d = 0; d < 6; ++d) C->w_grid[d] += wv[6 * mu + d];
+  free(wv);
+  free(T);
+  free(V);
+}
+
+/* Prolongation: e^{k,tot}_mu = e^k_mu + sum_nu phi^{k+1}_nu(X^k_mu) e^{k+1,tot}_nu,
+ * the fine node mu sitting at mu/2 in coarse units. */
+static void prolongate_level(ctx_t* C, int k) {
+  const int* nf = C->n[k];
+  const int* nc = C->n[k + 1];
+#pragma omp parallel for num_threads(NT) schedule(static)
+  for (long mu = 0; mu < C->np[k]; ++mu) {
+    long m0 = mu % nf[0], m1 = (mu / nf[0]) % nf[1], m2 = mu / ((long)nf[0] * nf[1]);
+    double p[3] = {0.5 * m0, 0.5 * m1, 0.5 * m2};
+    double acc = 0.0;
+    for (long v2 = (long)ceil(p[2] - 2.0); v2 <= (long)floor(p[2] + 2.0); ++v2)
+      for (long v1 = (long)ceil(p[1] - 2.0); v1 <= (long)floor(p[1] + 2.0); ++v1)
+        for (long v0 = (long)ceil(p[0] - 2.0); v0 <= (long)floor(p[0] + 2.0); ++v0) {
+          double w = orc_Phi(p[0] - v0) * orc_Phi(p[1] - v1) * orc_Phi(p[2] - v2);
+          if (w == 0.0) continue;
+          long idx = wrapi(v0, nc[0]) + nc[0] * (wrapi(v1, nc[1]) + nc[1] * wrapi(v2, nc[2]));
+          acc += w * C->et[k + 1][idx];
+        }
+    C->et[k][mu] = C->e[k][mu] + acc;
+  }
+}
+
+static void grid_pipeline(ctx_t* C) {
+  anterpolate(C);
+  for (int k = 1; k < C->l; ++k) restrict_level(C, k);
+  for (int k = 1; k < C->l; ++k) evaluate_level(C, k);
+  evaluate_top(C);
+  memcpy(C->et[C->l], C->e[C->l], sizeof(double) * (size_t)C->np[C->l]);
+  for (int k = C->l - 1; k >= 1; --k) prolongate_level(C, k);
+}
+
+/* Eq. (interpolation) and its gradient for atom i: e_i and grad e_i. */
+static void interpolate_atom(const ctx_t* C, int64_t i, double* ei, double g[3]) {
+  const int* n = C->n[1];
+  double u[3];
+  for (int d = 0; d < 3; ++d) u[d] = n[d] * C->s[3 * i + d];
+  double acc = 0.0, gs[3] = {0, 0, 0};
+  for (long m0 = (long)ceil(u[0] - 2.0); m0 <= (long)floor(u[0] + 2.0); ++m0)
+    for (long m1 = (long)ceil(u[1] - 2.0); m1 <= (long)floor(u[1] + 2.0); ++m1)
+      for (long m2 = (long)ceil(u[2] - 2.0); m2 <= (long)floor(u[2] + 2.0); ++m2) {
+        long idx = wrapi(m0, n[0]) + n[0] * (wrapi(m1, n[1]) + n[1] * wrapi(m2, n[2]));
+        double ev = C->et[1][idx];
+        double p0 = orc_Phi(u[0] - m0), p1 = orc_Phi(u[1] - m1), p2 = orc_Phi(u[2] - m2);
+        acc += p0 * p1 * p2 * ev;
+        gs[0] += n[0] * orc_dPhi(u[0] - m0) * p1 * p2 * ev;
+        gs[1] += n[1] * p0 * orc_dPhi(u[1] - m1) * p2 * ev;
+        gs[2] += n[2] * p0 * p1 * orc_dPhi(u[2] - m2) * ev;
+      }
+  *ei = acc;
+  /* d/dx_a = sum_d (d/ds_d) G[d][a] */
+  for (int a = 0; a < 3; ++a) g[a] = gs[0] * C->G[a] + gs[1] * C->G[3 + a] + gs[2] * C->G[6 + a];
+}
+
+static double c_self(double a) { return orc_gamma(0.0) / pow(a, 6.0); }
+
+/* ------------------------------------------------------------------ */
+/* Public entry points.                                                */
+/* ------------------------------------------------------------------ */
+
+int orc_eval(const double H[9], double a, const int n[3], int levels, double r_img, int64_t N,
+             const double* x, const double* c, double* E, double* F, double* W, double* eatom,
+             double* level_energy) {
+  ctx_t C;
+  int rc = ctx_init(&C, H, a, n, levels, r_img, N, x, c);
+  if (rc) {
+    ctx_free(&C);
+    return rc;
+  }
+  grid_pipeline(&C);
+  double* e0 = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+  double* fl = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+  double* wl = (double*)malloc(sizeof(double) * 6 * (size_t)(N > 0 ? N : 1));
+  double* eg = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+  double* fg = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+#pragma omp parallel for num_threads(NT) schedule(dynamic, 16)
+  for (int64_t i = 0; i < N; ++i) {
+    local_atom(&C, i, &e0[i], fl + 3 * i, wl + 6 * i);
+    double gx[3];
+    interpolate_atom(&C, i, &eg[i], gx);
+    for (int d = 0; d < 3; ++d) fg[3 * i + d] = c[i] * gx[d]; /* F = +c_i grad e */
+  }
+  double cs = c_self(a);
+  double El = 0.0, Es = 0.0, Et = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = 0; i < N; ++i) {
+    double epi = -0.5 * c[i] * (e0[i] + eg[i]) + 0.5 * cs * c[i] * c[i];
+    if (eatom) eatom[i] = epi;
+    El += -0.5 * c[i] * e0[i];
+    Es += 0.5 * cs * c[i] * c[i];
+    Et += epi;
+    if (F)
+      for (int d = 0; d < 3; ++d) F[3 * i + d] = fl[3 * i + d] + fg[3 * i + d];
+    for (int d = 0; d < 6; ++d) w[d] += wl[6 * i + d];
+  }
+  if (E) *E = Et;
+  if (W)
+    for (int d = 0; d < 6; ++d) W[d] = w[d] + C.w_grid[d];
+  if (level_energy) {
+    level_energy[0] = El;
+    level_energy[1] = Es;
+    for (int k = 1; k <= levels; ++k) {
+      double s = 0.0;
+      for (long mu = 0; mu < C.np[k]; ++mu) s += C.q[k][mu] * C.e[k][mu];
+      level_energy[1 + k] = -0.5 * s;
+    }
+    level_energy[levels + 2] = Et;
+  }
+  free(e0);
+  free(fl);
+  free(wl);
+  free(eg);
+  free(fg);
+  ctx_free(&C);
+  return 0;
+}
+
+int orc_eval_sample(const double H[9], double a, const int n[3], int levels, double r_img,
+                    int64_t N, const double* x, const double* c, int64_t n_idx,
+                    const int64_t* idx, double* F, double* eatom, double* grid_energy) {
+  ctx_t C;
+  int rc = ctx_init(&C, H, a, n, levels, r_img, N, x, c);
+  if (rc) {
+    ctx_free(&C);
+    return rc;
+  }
+  for (int64_t t = 0; t < n_idx; ++t)
+    if (idx[t] < 0 || idx[t] >= N) {
+      ctx_free(&C);
+      return -1;
+    }
+  grid_pipeline(&C);
+  double cs = c_self(a);
+#pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
+  for (int64_t t = 0; t < n_idx; ++t) {
+    int64_t i = idx[t];
+    double e0, fl[3], wl[6], eg, gx[3];
+    local_atom(&C, i, &e0, fl, wl);
+    interpolate_atom(&C, i, &eg, gx);
+    if (F)
+      for (int d = 0; d < 3; ++d) F[3 * t + d] = fl[d] + c[i] * gx[d];
+    if (eatom) eatom[t] = -0.5 * c[i] * (e0 + eg) + 0.5 * cs * c[i] * c[i];
+  }
+  if (grid_energy) {
+    double s = 0.0;
+    for (int k = 1; k <= levels; ++k)
+      for (long mu = 0; mu < C.np[k]; ++mu) s += C.q[k][mu] * C.e[k][mu];
+    *grid_energy = -0.5 * s;
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img, int64_t N,
+              const double* x, const double* c, double* out) {
+  ctx_t C;
+  int rc = ctx_init(&C, H, a, n, levels, r_img, N, x, c);
+  if (rc) {
+    ctx_free(&C);
+    return rc;
+  }
+  grid_pipeline(&C);
+  size_t off = 0;
+  for (int k = 1; k <= levels; ++k) {
+    size_t np = (size_t)C.np[k];
+    memcpy(out + off, C.q[k], np * sizeof(double));
+    memcpy(out + off + np, C.e[k], np * sizeof(double));
+    memcpy(out + off + 2 * np, C.et[k], np * sizeof(double));
+    off += 3 * np;
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+int orc_top_table(const double H[9], double a, const int nl[3], int levels, double r_img,
+                  double* T, double* V) {
+  double G[9];
+  if (inv3(H, G) || levels < 1 || !(a > 0.0)) return -1;
+  for (int d = 0; d < 3; ++d)
+    if (nl[d] < 1) return -2;
+  double R = default_radius(H, nl, levels, a, r_img);
+  top_tables(H, G, a, nl, levels, R, T, V);
+  return 0;
+}
+
+int orc_brute(const double H[9], double r_img, int64_t N, const double* x, const double* c,
+              double* E, double* F, double* W) {
+  double G[9];
+  if (inv3(H, G) || !(r_img > 0.0) || N < 0) return -1;
+  double vol = fabs(det3(H));
+  double R = r_img, A[3];
+  for (int d = 0; d < 3; ++d) A[d] = R * rownorm(G, d);
+  double* s = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) {
+    mv3(G, x + 3 * i, s + 3 * i);
+    for (int d = 0; d < 3; ++d) {
+      s[3 * i + d] -= floor(s[3 * i + d]);
+      if (s[3 * i + d] >= 1.0) s[3 * i + d] = 0.0;
+    }
+  }
+  double* ei = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+  double* fi = (double*)calloc(3 * (size_t)(N > 0 ? N : 1), sizeof(double));
+  double* wi = (double*)calloc(6 * (size_t)(N > 0 ? N : 1), sizeof(double));
+#pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
+  for (int64_t i = 0; i < N; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double ds[3] = {s[3 * j] - s[3 * i], s[3 * j + 1] - s[3 * i + 1], s[3 * j + 2] - s[3 * i + 2]};
+      long lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = (long)ceil(-A[d] - ds[d]);
+        hi[d] = (long)floor(A[d] - ds[d]);
+      }
+      double cc = c[i] * c[j];
+      for (long n0 = lo[0]; n0 <= hi[0]; ++n0)
+        for (long n1 = lo[1]; n1 <= hi[1]; ++n1)
+          for (long n2 = lo[2]; n2 <= hi[2]; ++n2) {
+            if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
+            double t[3] = {ds[0] + n0, ds[1] + n1, ds[2] + n2}, d3[3];
+            mv3(H, t, d3);
+            double r2 = d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2];
+            if (!(r2 < R * R)) continue;
+            double r6 = r2 * r2 * r2;
+            ei[i] += -0.5 * cc / r6;
+            double gp = -6.0 / (r6 * r2); /* (d/dr r^-6)/r */
+            for (int d = 0; d < 3; ++d) fi[3 * i + d] -= cc * gp * d3[d];
+            add_outer(wi + 6 * i, 0.5 * cc * gp, d3);
+          }
+    }
+  }
+  double csum = 0.0;
+  for (int64_t i = 0; i < N; ++i) csum += c[i];
+  double tailE = 4.0 * M_PI / (3.0 * R * R * R * vol);
+  double tailV = -8.0 * M_PI / (3.0 * R * R * R * vol);
+  double e = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = 0; i < N; ++i) {
+    e += ei[i];
+    for (int d = 0; d < 6; ++d) w[d] += wi[6 * i + d];
+  }
+  e += -0.5 * csum * csum * tailE;
+  for (int d = 0; d < 3; ++d) w[d] += 0.5 * csum * csum * tailV;
+  if (E) *E = e;
+  if (F) memcpy(F, fi, sizeof(double) * 3 * (size_t)N);
+  if (W) memcpy(W, w, sizeof(w));
+  free(s);
+  free(ei);
+  free(fi);
+  free(wi);
+  return 0;
+}

@@ -1,0 +1,90 @@
+/*
+ * mls6_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow FP64 CPU implementation of multilevel summation (MLS) for the
+ * r^-6 dispersion kernel (Tameling, Springer, Bientinesi, Ismail, "Multilevel
+ * Summation for Dispersion", arXiv 1308.4005).  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it; the GPU
+ * library never calls, links or includes anything from this directory.
+ *
+ * Conventions (shared by the whole oracle):
+ *   - The periodic cell is a 3x3 matrix H (row-major); its COLUMNS are the
+ *     lattice vectors, x = H s with fractional s in [0,1)^3.  An orthorhombic
+ *     box is H = diag(Lx, Ly, Lz).  Grids deform with the cell: grid node mu
+ *     on a level with n points per axis sits at X_mu = H (mu / n).
+ *   - Physical energy  E = -1/2 sum_i sum_{j,n}' c_i c_j |x_i - x_j + H n|^-6,
+ *     i.e. the quadratic form of Eq. (pot-vec-mat-vec) with xi = c (Sec. II.D,
+ *     geometric mixing, c_i = sqrt(C6_i)), halved for the double sum and with
+ *     the attractive sign of Eq. (disp-pair-pot).  Forces F = -dE/dx.
+ *   - Virial W_ab = -dE/d(eps_ab) under the affine strain H -> (I+eps) H with
+ *     fractional coordinates (atoms and grid nodes) held fixed.
+ *     Order of the six components: xx, yy, zz, xy, xz, yz.
+ *   - Grid arrays are x-fastest: index = i + n0*(j + n1*k).
+ */
+#ifndef MLS6_ORACLE_H
+#define MLS6_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Closed forms (Sec. II.A.3-5). */
+double orc_gamma(double rho);                 /* Eq. (gamma) */
+double orc_dgamma(double rho);                /* d gamma / d rho */
+double orc_gk(int k, int l, double a, double r);   /* Eqs. (g_0), (g_k), (g_l) */
+double orc_dgk(int k, int l, double a, double r);  /* d g_k / dr */
+double orc_Phi(double t);                     /* Eq. (Phi-Hermite) */
+double orc_dPhi(double t);                    /* d Phi / dt */
+
+/* Finest-grid size: per axis the multiple of 2^(levels-1) nearest to L/h
+ * (ties to the finer grid), at least 2^(levels-1).  Returns 0 on success. */
+int orc_grid_dims(const double L[3], double h, int levels, int n_out[3]);
+
+/* Number of doubles orc_eval writes to level_energy: levels + 3
+ * ([0] local part, [1] self term, [2..levels+1] per-level grid energies
+ *  -1/2 q^k . e^k, [levels+2] total). */
+
+/* Full MLS evaluation.  x: N*3 Cartesian positions, c: N coefficients.
+ * Any output pointer may be NULL.  F: N*3, W: 6, eatom: N (per-atom energy
+ * -1/2 c_i (e0_i + e_i) + 1/2 c_self c_i^2, which sums to E),
+ * level_energy: levels+3 values as described above.
+ * r_img: radius (absolute length) of the direct image sum for the coarsest
+ * level table; <= 0 selects 64 * (largest cell-column length).
+ * Returns 0 on success, <0 on bad arguments. */
+int orc_eval(const double H[9], double a, const int n[3], int levels, double r_img,
+             int64_t N, const double* x, const double* c,
+             double* E, double* F, double* W, double* eatom, double* level_energy);
+
+/* Same evaluation restricted to the atoms listed in idx (n_idx of them):
+ * F (n_idx*3) and eatom (n_idx) for those atoms only; grid_energy receives
+ * the grid part -1/2 sum_k q^k.e^k (all atoms).  The local part is computed
+ * only for the listed atoms, so this is usable at large N. */
+int orc_eval_sample(const double H[9], double a, const int n[3], int levels, double r_img,
+                    int64_t N, const double* x, const double* c,
+                    int64_t n_idx, const int64_t* idx,
+                    double* F, double* eatom, double* grid_energy);
+
+/* Stage export: writes, level after level, q^k, e^k and e^{k,tot} (each of
+ * n_k points) for k = 1..levels into out (3 * sum_k n_k doubles). */
+int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img,
+              int64_t N, const double* x, const double* c, double* out);
+
+/* Coarsest-level periodic tables: T (n_l points) and the six virial tables
+ * V_ab (6 * n_l, component-major), for a coarsest grid of nl points. */
+int orc_top_table(const double H[9], double a, const int nl[3], int levels, double r_img,
+                  double* T, double* V);
+
+/* Exact periodic sum by direct image summation out to radius r_img plus the
+ * continuum tail.  Any output may be NULL.  F: N*3, W: 6. */
+int orc_brute(const double H[9], double r_img, int64_t N, const double* x, const double* c,
+              double* E, double* F, double* W);
+
+/* OpenMP threads used by the loops above (<=0: library default). */
+void orc_set_threads(int n);
+int  orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
