@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Throughput benchmark of multilevel summation for r^-6 dispersion on GB300.
+
+One step = one full ``mls6_eval`` (bin, local pair part, anterpolation,
+restriction, level stencils, coarsest level, prolongation, interpolation,
+energy/virial reduction) of the 65,536-atom liquid/vacuum slab (40x40x51.2
+slab at rho=0.8 in a periodic 40x40x120 box, C6 in [0.8,1.2], a=3, h=1.25,
+4 levels, FP32 with FP64 energy/virial).  Metric: atom-evals/s (atoms whose
+energy contribution and force one evaluation produces, per second).
+
+  --impl ours        (default) the CUDA library through its C ABI
+  --impl reference   the FP64 CPU oracle on the host cores (bounded sample)
+
+Under torchrun each rank evaluates an independent replica (different seed)
+on its own GPU; value = atoms of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2   # GB300 FP64 issue rate per SM per clock (FMA lanes)
+SMS = 152
+# Floating-point operations counted per unit of algorithmic work (fixed
+# tallies, see the design notes):
+FLOP_PAIR = 42          # one pair inside the cutoff: energy + force
+FLOP_PAIR_VIR = 12      # ... plus the six virial products
+FLOP_TAP = 2            # one stencil tap (multiply-add) per node
+FLOP_TAP_VIR = 12       # ... plus six virial multiply-adds
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="slab65536")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dwell", type=float, default=1.5,
+                    help="seconds of untimed back-to-back evaluations before timing")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+_REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+                0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+                0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons (read only)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,utilization.gpu,power.draw,clocks_event_reasons.active")
+
+    def __init__(self, gpu_id):
+        self.samples = []
+        self.err = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # nvidia-smi missing
+            self.p = None
+            self.err = repr(e)
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 5:
+                continue
+            try:
+                sm, smax, util = float(parts[0]), float(parts[1]), float(parts[2])
+                reasons = int(parts[4], 16)
+            except ValueError:
+                continue
+            self.samples.append((time.time(), sm, smax, util, reasons))
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self, t0, t1):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": self.err}
+        win = [s for s in self.samples if t0 <= s[0] <= t1]
+        load = [s for s in win if s[3] > 0] or win
+        if not load:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for s in load:
+            for bit, name in _REASON_BITS.items():
+                if s[4] & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[1] for s in load),
+                "sm_max_mhz": max(s[2] for s in load),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+# ---------------------------------------------------------- distributed
+
+def dist_setup(torch):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def reduce_max(torch, value, world, device):
+    if world == 1:
+        return value
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------- workload
+
+def workload_arrays(name, rank, precision):
+    import numpy as np
+
+    from paper_1308_4005_gb300 import inputs as I
+
+    w = I.workload(name)
+    if rank:
+        import dataclasses
+
+        w = dataclasses.replace(w, seed=w.seed + 1000 * rank)
+    x, c = I.generate(w)
+    dt = np.float32 if precision == "fp32" else np.float64
+    return w, x.astype(dt), c.astype(dt)
+
+
+def count_pairs(x, box, a):
+    """Ordered pairs (i, j) with periodic distance < a (the pair kernel's
+    algorithmic work)."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+
+    xx = np.mod(np.asarray(x, dtype=np.float64), box)
+    p = cKDTree(xx, boxsize=box).query_pairs(a, output_type="ndarray")
+    return 2 * int(p.shape[0])
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def _oracle_parts(O, w, xd, cd, S, rng):
+    """Seconds for the oracle's grid part (all atoms) and for its local part
+    over S random atoms."""
+    import numpy as np
+
+    n = O.grid_dims(w.box, w.h, w.levels)
+    t0 = time.perf_counter()
+    O.evaluate_sample(w.box, w.a, n, w.levels, xd, cd, np.zeros(0, np.int64))
+    t_grid = time.perf_counter() - t0
+    idx = rng.choice(w.N, S, replace=False)
+    t0 = time.perf_counter()
+    O.local(w.box, w.a, xd, cd, idx)
+    t_loc = time.perf_counter() - t0
+    return t_grid, t_loc
+
+
+def oracle_baseline(w, x, c, budget_s=15.0):
+    """Time the FP64 oracle on the host cores on a bounded sample: the whole
+    grid part (anterpolation .. interpolation, all atoms) once, and the local
+    part for a random sample of S atoms; the full-evaluation time is
+    t_grid + t_local(S) * N / S."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    xd, cd = np.asarray(x, np.float64), np.asarray(c, np.float64)
+    rng = np.random.default_rng(7)
+    S = min(w.N, 256)
+    t_grid, t_loc = _oracle_parts(O, w, xd, cd, S, rng)
+    S2 = int(min(w.N, max(S, S * max(budget_s - t_grid, 1.0) / max(t_loc, 1e-6))))
+    t_grid, t_loc2 = _oracle_parts(O, w, xd, cd, S2, rng)
+    t_full = t_grid + t_loc2 * w.N / S2
+    return {"value": w.N / t_full, "unit": "atom-evals/s", "cores": O.threads(),
+            "kind": "oracle",
+            "sample": (f"FP64 oracle, {w.name}: grid part for all {w.N} atoms "
+                       f"({t_grid:.2f} s) + local part for {S2} random atoms ({t_loc2:.2f} s), "
+                       f"full evaluation extrapolated to {t_full:.1f} s")}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from oracle import oracle as O
+
+    w, x, c = workload_arrays(args.workload, 0, args.precision)
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    xd, cd = np.asarray(x, np.float64), np.asarray(c, np.float64)
+    rng = np.random.default_rng(11)
+    S = min(w.N, max(1, w.N // 32))
+    for _ in range(args.warmup):
+        _oracle_parts(O, w, xd, cd, S, rng)
+    full, tg = [], []
+    for _ in range(args.steps):
+        t_grid, t_loc = _oracle_parts(O, w, xd, cd, S, rng)
+        tg.append(t_grid)
+        full.append(t_grid + t_loc * w.N / S)
+    ms = 1e3 * statistics.mean(full)
+    value = w.N / (ms / 1e3)
+    line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(w, args, world),
+            "cpu_baseline": {"value": value, "unit": "atom-evals/s", "cores": O.threads(),
+                             "kind": "oracle",
+                             "sample": (f"each step: FP64 oracle grid part for all {w.N} atoms "
+                                        f"(mean {statistics.mean(tg):.2f} s) + local part for "
+                                        f"{S} random atoms, extrapolated to all {w.N}")},
+            "e2e": {"value": value, "unit": "atom-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, args, world):
+    return {"workload": w.name, "N_per_gpu": w.N, "box": list(w.box), "a": w.a, "h": w.h,
+            "levels": w.levels, "order": 3, "precision": args.precision,
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1308_4005_gb300 import build as B
+    from paper_1308_4005_gb300 import mls6
+
+    world, rank, local = dist_setup(torch)
+    assert torch.cuda.is_available(), "bench.py --impl ours needs a GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    mls6.load()
+    w, x, c = workload_arrays(args.workload, rank, args.precision)
+    dt = torch.float32 if args.precision == "fp32" else torch.float64
+    esz = 4 if args.precision == "fp32" else 8
+    N = w.N
+    stream = torch.cuda.Stream(device=dev)
+    plan = mls6.Plan(w.box, N, w.a, w.h, w.levels, precision=args.precision,
+                     stream=stream.cuda_stream)
+    info = plan.info()
+    pos_h = torch.tensor(np.c_[x, c], dtype=dt).pin_memory()
+    pos = torch.empty((N, 4), dtype=dt, device=dev)
+    F = torch.empty((N, 3), dtype=dt, device=dev)
+    F_h = torch.empty((N, 3), dtype=dt).pin_memory()
+    out = torch.zeros(8, dtype=torch.float64, device=dev)
+    out_h = torch.zeros(8, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        pos.copy_(pos_h, non_blocking=True)
+    stream.synchronize()
+
+    def step():
+        rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), out.data_ptr(),
+                            out.data_ptr() + 8)
+        if rc:
+            raise mls6.MLS6Error(rc, "mls6_eval")
+
+    sampler = ClockSampler(gpu_smi_id(torch, local))
+    t_dwell0 = time.time()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        stream.synchronize()
+        t_end = time.time() + args.dwell
+        while time.time() < t_end:
+            for _ in range(50):
+                step()
+            stream.synchronize()
+    rc = mls6.mls6_last_error(plan.handle)
+    if rc:
+        raise mls6.MLS6Error(rc, "warmup")
+
+    # ------------------------------------------------ timed region (device)
+    mls6.mls6_profile(plan.handle, True)
+    stage_acc = {}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_timed0 = time.time()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            st, nl = mls6.mls6_stage_times(plan.handle)  # waits for this step
+            launches += nl
+            for name, ms in st.items():
+                stage_acc[name] = stage_acc.get(name, 0.0) + ms
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t_timed1 = time.time()
+    mls6.mls6_profile(plan.handle, False)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    total_ms = reduce_max(torch, total_ms, world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * N * args.steps / (total_ms / 1e3)
+    stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
+    E_dev = float(out[0].item())
+
+    # --------------------------------------------- end-to-end (host buffers)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev2[k][0].record(stream)
+            pos.copy_(pos_h, non_blocking=True)
+            step()
+            F_h.copy_(F, non_blocking=True)
+            out_h.copy_(out, non_blocking=True)
+            ev2[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e2e_ms = reduce_max(torch, sum(a.elapsed_time(b) for a, b in ev2), world, dev)
+    e2e_value = world * N * args.steps / (e2e_ms / 1e3)
+    t_e2e1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_dwell0, t_e2e1)
+    clocks["window"] = "warm-up dwell + timed steps (the timed region alone is shorter than the sampling period)"
+
+    # ------------------------------------------------------------- roofline
+    n_pairs = count_pairs(x, np.array(w.box), w.a)
+    lv = info["n_grid"]
+    nodes_lt = sum(n[0] * n[1] * n[2] for n in lv[:-1])
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    work = {
+        "pair": ("alu", n_pairs * (FLOP_PAIR + FLOP_PAIR_VIR) / 1e12, "TFLOP/s",
+                 f"{n_pairs} ordered pairs inside a x {FLOP_PAIR + FLOP_PAIR_VIR} flop"),
+        "stencil": ("alu", nodes_lt * info["ntaps"] * (FLOP_TAP + FLOP_TAP_VIR) / 1e12,
+                    "TFLOP/s", f"{nodes_lt} nodes on levels < l x {info['ntaps']} taps x "
+                               f"{FLOP_TAP + FLOP_TAP_VIR} flop"),
+        "interpolate": ("hbm", (N * (16 + 4 + esz + 3 * esz + 3 * esz) + lv[0][0] * lv[0][1] *
+                                lv[0][2] * esz) / 1e9, "GB/s",
+                        "per atom: sorted record, index, e0, local force in, force out; grid once"),
+        "anterpolate": ("hbm", (N * 16 + lv[0][0] * lv[0][1] * lv[0][2] * esz) / 1e9, "GB/s",
+                        "per atom: sorted record; finest grid written once"),
+        "bin": ("hbm", N * (16 + 16 + 4 + 4 + 16 + 4 + 16 + 4) / 1e9, "GB/s",
+                "read input, write wrapped record + cell id, scatter read/write, sort"),
+    }
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    roof = None
+    if dom in work:
+        bound, amount, unit, note = work[dom]
+        ach = amount / (stage_ms[dom] / 1e3)
+        if bound == "alu":
+            peak, peak_note = fp32_peak, (f"FP32 FMA peak derived: {SMS} SMs x "
+                                          f"{FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                          "(median sampled SM clock)")
+        else:
+            peak, peak_note = hbm_peak(), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+        roof = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak, "traffic": None, "work": note, "peak_source": peak_note,
+                "avg_launch_ms": stage_ms[dom]}
+    line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": config_of(w, args, world),
+            "e2e": {"value": e2e_value, "unit": "atom-evals/s",
+                    "h2d_bytes_per_step": int(pos_h.numel() * pos_h.element_size()),
+                    "d2h_bytes_per_step": int(F_h.numel() * F_h.element_size() + 8 * 8)},
+            "gpu_launches": int(launches),
+            "roofline": roof, "stages_ms": stage_ms, "clocks": clocks,
+            "energy": E_dev}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(w, x, c)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * mls6.h -- C ABI of the GB300 (sm_103a) multilevel summation library for
+ * r^-6 dispersion.
+ *
+ * Method: Tameling, Springer, Bientinesi, Ismail, "Multilevel Summation for
+ * Dispersion: A Linear-Time Algorithm for r^-6 Potentials", arXiv 1308.4005.
+ * The kernel 1/r^6 is split (Eq. complete-splitting) into a local part g_0
+ * (cutoff a, evaluated as a cell-list pair sum) and grid parts g_1..g_l that
+ * are anterpolated to the finest grid, restricted, evaluated per level
+ * (cutoff stencil 2^k a on levels k < l, periodic all-to-all table on level
+ * l), prolongated and interpolated back (Sec. II.B), minus the self term
+ * gamma(0)/a^6 xi^T xi (Eq. self-interaction-energy).
+ *
+ * Conventions
+ *   energy  E = -1/2 sum_i sum_{j,n}' c_i c_j |x_i - x_j + n L|^-6  (MLS
+ *           approximation of it), i.e. the quadratic form of
+ *           Eq. (pot-vec-mat-vec) with xi = c (geometric mixing,
+ *           Eqs. xi-general / xi-lj-geometric, c_i = sqrt(C6_i)), halved for
+ *           the double sum and with the attractive sign of Eq. (disp-pair-pot).
+ *   forces  F_i = -dE/dx_i, the exact gradient of the MLS energy (the paper
+ *           does not print a force formula).
+ *   virial  W_ab = -dE/d eps_ab under the affine strain x -> (1+eps) x of
+ *           atoms, box and grids; six doubles in the order xx yy zz xy xz yz.
+ *   box     orthorhombic and periodic in all three directions (Sec. II.C:
+ *           only periodic boundaries are treated).
+ *   grids   level k (1..l) has n_k = n_1 / 2^(k-1) points per axis and
+ *           spacing h_k = 2^(k-1) L/n_1; node mu sits at mu * h_k.  n_1 is,
+ *           per axis, the multiple of 2^(l-1) nearest to L/h (ties to the
+ *           finer grid) -- non-power-of-two grids are allowed (Sec. III.C).
+ *   basis   the cubic Hermite Phi of Eq. (Phi-Hermite), interpolation order
+ *           p = 3 (the only order implemented).
+ *
+ * Threading and streams: a plan is not thread-safe; calls on one plan must
+ * be serialised by the caller.  Work is enqueued on the plan's stream (the
+ * legacy default stream unless mls6_set_stream was called).
+ * Errors are returned as negative mls6_status codes; nothing aborts and
+ * there is no CPU fallback: without a usable CUDA device every call that
+ * needs one returns MLS6_ERR_CUDA.
+ */
+#ifndef MLS6_H
+#define MLS6_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mls6_plan_t mls6_plan_t;
+
+typedef enum {
+  MLS6_OK = 0,
+  MLS6_ERR_ARG = -1,        /* NULL pointer, N < 0, a <= 0, h <= 0, bad level ... */
+  MLS6_ERR_GRID = -2,       /* grid sizes not nested / too many levels */
+  MLS6_ERR_BOX = -3,        /* non-positive or non-finite box */
+  MLS6_ERR_ORDER = -4,      /* interpolation order other than 3 */
+  MLS6_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error) */
+  MLS6_ERR_NOMEM = -6,      /* device allocation failed */
+  MLS6_ERR_TIMEOUT = -7,    /* reserved for bounded device waits */
+  MLS6_ERR_NONFINITE = -8,  /* a position or coefficient was NaN/Inf */
+  MLS6_ERR_SIZE = -9        /* request larger than a fixed capacity */
+} mls6_status;
+
+typedef enum {
+  MLS6_FP64 = 0,  /* every step in double precision */
+  MLS6_FP32 = 1   /* pair kernel and grids in float; coarsest level, energy
+                     and virial accumulation in double */
+} mls6_precision;
+
+/* Finest-grid size for a box (per axis the multiple of 2^(levels-1) nearest
+ * to L/h, ties to the finer grid).  Host only; needs no GPU.
+ * box: 3 doubles (Lx, Ly, Lz).  n_out: 3 ints.  Returns MLS6_OK or an error. */
+int mls6_grid_dims(const double box[3], double h, int levels, int n_out[3]);
+
+/* Coarsest-level periodic tables (Eqs. last-grid-periodic and
+ * last-grid-periodic-transformed): T[m] = sum_{n in Z^3} g_l(|m h_l + n L|)
+ * for the nl[0] x nl[1] x nl[2] offsets m (x fastest), and the virial tables
+ * V[c * n_l + m] = sum_n g_l'(r)/r r_a r_b for the six components c.  The
+ * lattice sums are evaluated by Ewald summation of r^-6.  Host only; needs
+ * no GPU.  T: nl0*nl1*nl2 doubles, V: 6 times that (may be NULL). */
+int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double a, double* T,
+                       double* V);
+
+/* Create a plan: validates the parameters, computes the grid hierarchy and
+ * every table on the host in FP64, and allocates all device workspace (the
+ * plan owns it).  box: 3 doubles.  N: number of atoms (>= 0), fixed for the
+ * plan.  a: local cutoff (> 0).  h: requested finest spacing (> 0).
+ * levels: number of grid levels l (1..12).  order: interpolation order, 3.
+ * precision: mls6_precision.  *out receives the plan (NULL on error). */
+int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
+              int order, int precision);
+
+/* Enqueue subsequent work of the plan on a cudaStream_t (NULL = legacy
+ * default stream). */
+int mls6_set_stream(mls6_plan_t* p, void* stream);
+
+/* Evaluate energy, forces and virial.
+ *   pos     device pointer, N rows of the plan's precision (double or float):
+ *           if c == NULL each row is {x, y, z, c} (4 values), otherwise
+ *           {x, y, z} (3 values).  Positions may lie anywhere; they are
+ *           wrapped into the box.  Read only.
+ *   c       device pointer to N coefficients c_i = sqrt(C6_i) (plan
+ *           precision) or NULL (coefficients in the 4th column of pos).
+ *   forces  device pointer, N x 3 of the plan precision, overwritten.
+ *   energy  one double, host or device pointer, or NULL to skip.
+ *   virial  six doubles (xx yy zz xy xz yz), host or device, or NULL to skip
+ *           (skipping it also skips the virial arithmetic).
+ * The call is asynchronous on the plan's stream unless energy or virial is a
+ * host pointer, in which case it returns after the stream has finished.
+ * NaN/Inf inputs are detected on the device; the status is reported by the
+ * call when it synchronises, else by mls6_last_error.  N = 0 gives E = 0. */
+int mls6_eval(mls6_plan_t* p, const void* pos, const void* c, void* forces, double* energy,
+              double* virial);
+
+/* As mls6_eval, and also writes the per-atom energies
+ * -1/2 c_i (e0_i + e_i) + 1/2 (gamma(0)/a^6) c_i^2 (they sum to E) to the
+ * device array atom_energy (N doubles). */
+int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces, double* energy,
+                    double* virial, double* atom_energy);
+
+/* Waits for the plan's stream and returns the first device-detected error of
+ * the last evaluation (MLS6_ERR_NONFINITE) or a pending CUDA error. */
+int mls6_last_error(mls6_plan_t* p);
+
+/* Plan geometry.  n_grid: 3*levels ints (points per axis, per level), may
+ * be NULL; h_actual: 3 doubles (finest spacing), may be NULL; levels: may be
+ * NULL; ntaps: number of stencil taps per level k < l, may be NULL. */
+int mls6_plan_info(const mls6_plan_t* p, int* n_grid, double* h_actual, int* levels, int* ntaps);
+
+/* Copy one grid of the last evaluation to host memory as doubles (x fastest):
+ * which = 0: xi^k (anterpolated / restricted coefficients),
+ *         1: e^k (level evaluation), 2: e^{k,tot} (after prolongation).
+ * level: 1..l.  Synchronises the plan's stream. */
+int mls6_debug_grid(mls6_plan_t* p, int level, int which, double* host_out);
+
+/* Per-stage timing with CUDA events on the plan's stream (off by default).
+ * While enabled, every evaluation records an event at each stage boundary:
+ * 0 bin (wrap, cell histogram, scan, scatter, per-cell order), 1 pair
+ * (local part), 2 anterpolation, 3 restriction, 4 level stencils,
+ * 5 coarsest level, 6 prolongation, 7 interpolation/forces, 8 reduction. */
+int mls6_profile(mls6_plan_t* p, int enable);
+
+/* Waits for the plan's stream and writes the stage durations of the last
+ * profiled evaluation (milliseconds) to ms[0..min(cap, stages)-1]; returns
+ * the number of stages (>= 0) or an error.  *launches (may be NULL)
+ * receives the number of kernels the last evaluation launched. */
+int mls6_stage_times(mls6_plan_t* p, double* ms, int cap, int* launches);
+
+/* Name of stage i (see mls6_profile), or NULL. */
+const char* mls6_stage_name(int i);
+
+/* Release the plan and all its device memory.  NULL is ignored. */
+void mls6_destroy(mls6_plan_t* p);
+
+/* Static description of a status code. */
+const char* mls6_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLS6_H */

@@ -21,7 +21,8 @@
  *  R6 periodic basis functions and kernels are sums over images, which
  *     wrapping node indices with repetition reproduces on small grids.
  *  R7 the coarsest-level table (Eq. last-grid-periodic-transformed) is a
- *     direct image sum out to a radius R plus the continuum tail beyond R.
+ *     direct image sum under a smooth erfc window plus the integral of the
+ *     windowed-out remainder (compensated summation over the images).
  *  R8 virial: strain derivative with grids deforming with the cell.
  *  R9 cutoff tests are strict (r < cutoff); g_k is exactly 0 beyond.
  */
@@ -172,28 +173,88 @@ static void add_outer(double w[6], double s, const double d[3]) {
 /* Problem context.                                                    */
 /* ------------------------------------------------------------------ */
 
-/* Image radius of the coarsest-level table.  Given r_img > 0 it is used as
- * is; otherwise 64 times the longest cell vector, reduced for large
- * coarsest grids so that (points) x (images) stays near 3e7 (successive
- * doublings of R at 64 L change the table by ~1e-10 relative).  Never below
- * twice 2^(l-1) a, so that g_l = r^-6 beyond R and the tail is exact in
- * the continuum limit. */
+/* ------------------------------------------------------------------ */
+/* Lattice sums over periodic images (reading R7).                     */
+/*                                                                     */
+/* sum_n f(|x + H n|) for a radial f that equals r^-6 beyond R_in is   */
+/* split with the smooth window w(r) = erfc((r - Rm)/s)/2 into         */
+/*   sum_n f w          (direct sum over the images with r < Rm + 7s)  */
+/* + sum_n f (1 - w)    (replaced by its integral over space / det H). */
+/* 1 - w vanishes (to 1e-23) below Rm - 7s = R_in, so the complement   */
+/* is the smooth function r^-6 (1 - w) and its lattice sum equals the  */
+/* integral up to Poisson aliasing terms that fall like a Gaussian in  */
+/* s / (cell length); w vanishes (to 1e-23) beyond Rm + 7s.            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  double Rin, Rm, s, Rout;
+} window_t;
+
+/* Compensated (Neumaier) summation for the long image sums. */
+typedef struct {
+  double s, c;
+} ksum_t;
+
+static void kadd(ksum_t* k, double x) {
+  double t = k->s + x;
+  if (fabs(k->s) >= fabs(x))
+    k->c += (k->s - t) + x;
+  else
+    k->c += (x - t) + k->s;
+  k->s = t;
+}
+
+static double kval(const ksum_t* k) { return k->s + k->c; }
+
+static window_t make_window(double Rin, double Rout) {
+  window_t w;
+  w.Rin = Rin;
+  w.Rout = Rout;
+  w.s = (Rout - Rin) / 14.0;
+  w.Rm = Rin + 7.0 * w.s;
+  return w;
+}
+
+static double win(const window_t* w, double r) { return 0.5 * erfc((r - w->Rm) / w->s); }
+
+static double dwin(const window_t* w, double r) {
+  double u = (r - w->Rm) / w->s;
+  return -exp(-u * u) / (w->s * sqrt(M_PI));
+}
+
+/* (1/vol) int_{|x| > Rin} |x|^-6 (1 - w(|x|)) d^3x by Simpson's rule on
+ * [Rin, Rout] plus the exact remainder 4 pi / (3 Rout^3). */
+static double window_tail(const window_t* w, double vol) {
+  const int n = 20000;
+  double h = (w->Rout - w->Rin) / n, acc = 0.0;
+  for (int i = 0; i <= n; ++i) {
+    double r = w->Rin + i * h;
+    double f = 0.5 * erfc((w->Rm - r) / w->s) / (r * r * r * r);
+    acc += (i == 0 || i == n) ? f : ((i & 1) ? 4.0 * f : 2.0 * f);
+  }
+  return 4.0 * M_PI * (acc * h / 3.0 + 1.0 / (3.0 * w->Rout * w->Rout * w->Rout)) / vol;
+}
+
+/* Outer radius of the coarsest-level image sum.  Given r_img > 0 it is used
+ * as is; otherwise Rin + 21 L (window width s = 1.5 L, L the longest cell
+ * vector), reduced for large coarsest grids so that (points) x (images)
+ * stays near 3e7, but never below Rin + 7 L. */
 static double default_radius(const double H[9], const int nl[3], int levels, double a,
                              double r_img) {
-  double Lmax = 0.0;
+  double Rin = ldexp(a, levels - 1), vol = fabs(det3(H)), L = 0.0;
   for (int col = 0; col < 3; ++col) {
     double v = sqrt(H[col] * H[col] + H[3 + col] * H[3 + col] + H[6 + col] * H[6 + col]);
-    if (v > Lmax) Lmax = v;
+    if (v > L) L = v;
   }
   double R = r_img;
   if (!(R > 0.0)) {
     double np = (double)nl[0] * nl[1] * nl[2];
-    double f = cbrt(3.0e7 / (4.19 * np));
-    if (f > 64.0) f = 64.0;
-    if (f < 12.0) f = 12.0;
-    R = f * Lmax;
+    double cap = cbrt(3.0e7 * vol / (4.19 * np));
+    R = Rin + 21.0 * L;
+    if (R > cap) R = cap;
+    if (R < Rin + 7.0 * L) R = Rin + 7.0 * L;
   }
-  if (R < 2.0 * ldexp(a, levels - 1)) R = 2.0 * ldexp(a, levels - 1);
+  if (R < 2.0 * Rin) R = 2.0 * Rin;
   return R;
 }
 
@@ -411,16 +472,18 @@ static void evaluate_level(ctx_t* C, int k) {
 }
 
 /* Eq. (last-grid-periodic-transformed): T(m) = sum_{n in Z^3} g_l(|H(m/n_l + n)|),
- * by direct summation over |.| < R plus the continuum tail: beyond R,
- * g_l(r) = r^-6 and the lattice sum is replaced by its integral
- * (1/det H) int_{r>R} r^-6 d^3r = 4 pi / (3 R^3 det H).  The virial table
- * V(m) = sum_n g_l'(r)/r r (x) r gets the tail -8 pi/(3 R^3 det H) * delta. */
+ * with the windowed split above (g_l = r^-6 beyond Rin = 2^(l-1) a).  The
+ * virial table V(m) = sum_n g_l'(r)/r r (x) r is the strain derivative of
+ * the same split: the windowed part differentiates term by term, the
+ * complement (an integral over space divided by det H) contributes
+ * -delta_ab times itself. */
 static void top_tables(const double H[9], const double G[9], double a, const int nl[3],
                        int l, double R, double* T, double* V) {
   long np = (long)nl[0] * nl[1] * nl[2];
   double vol = fabs(det3(H));
-  double tailE = 4.0 * M_PI / (3.0 * R * R * R * vol);
-  double tailV = -8.0 * M_PI / (3.0 * R * R * R * vol);
+  window_t wd = make_window(ldexp(a, l - 1), R);
+  double tailE = window_tail(&wd, vol);
+  double tailV = -tailE;
   double A[3];
   for (int d = 0; d < 3; ++d) A[d] = R * rownorm(G, d);
 #pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
@@ -432,7 +495,7 @@ static void top_tables(const double H[9], const double G[9], double a, const int
       lo[d] = (long)ceil(-A[d] - t0[d]);
       hi[d] = (long)floor(A[d] - t0[d]);
     }
-    double acc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+    ksum_t acc = {0, 0}, v[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (long i0 = lo[0]; i0 <= hi[0]; ++i0)
       for (long i1 = lo[1]; i1 <= hi[1]; ++i1)
         for (long i2 = lo[2]; i2 <= hi[2]; ++i2) {
@@ -440,12 +503,21 @@ static void top_tables(const double H[9], const double G[9], double a, const int
           mv3(H, f, r3);
           double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
           if (!(r < R)) continue;
-          acc += orc_gk(l, l, a, r);
-          if (r > 0.0) add_outer(v, orc_dgk(l, l, a, r) / r, r3);
+          double g = orc_gk(l, l, a, r), wv = win(&wd, r);
+          kadd(&acc, g * wv);
+          if (r > 0.0) {
+            double gp = (orc_dgk(l, l, a, r) * wv + g * dwin(&wd, r)) / r;
+            kadd(&v[0], gp * r3[0] * r3[0]);
+            kadd(&v[1], gp * r3[1] * r3[1]);
+            kadd(&v[2], gp * r3[2] * r3[2]);
+            kadd(&v[3], gp * r3[0] * r3[1]);
+            kadd(&v[4], gp * r3[0] * r3[2]);
+            kadd(&v[5], gp * r3[1] * r3[2]);
+          }
         }
-    T[m] = acc + tailE;
+    T[m] = kval(&acc) + tailE;
     if (V) {
-      for (int d = 0; d < 6; ++d) V[d * np + m] = v[d] + (d < 3 ? tailV : 0.0);
+      for (int d = 0; d < 6; ++d) V[d * np + m] = kval(&v[d]) + (d < 3 ? tailV : 0.0);
     }
   }
 }
@@ -631,6 +703,32 @@ int orc_eval_sample(const double H[9], double a, const int n[3], int levels, dou
   return 0;
 }
 
+int orc_local(const double H[9], double a, int64_t N, const double* x, const double* c,
+              int64_t n_idx, const int64_t* idx, double* e0, double* F) {
+  ctx_t C;
+  int n1[3] = {1, 1, 1};
+  int rc = ctx_init(&C, H, a, n1, 1, 1.0, N, x, c);
+  if (rc) {
+    ctx_free(&C);
+    return rc;
+  }
+  for (int64_t t = 0; t < n_idx; ++t)
+    if (idx[t] < 0 || idx[t] >= N) {
+      ctx_free(&C);
+      return -1;
+    }
+#pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
+  for (int64_t t = 0; t < n_idx; ++t) {
+    double e, f[3], w[6];
+    local_atom(&C, idx[t], &e, f, w);
+    if (e0) e0[t] = e;
+    if (F)
+      for (int d = 0; d < 3; ++d) F[3 * t + d] = f[d];
+  }
+  ctx_free(&C);
+  return 0;
+}
+
 int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img, int64_t N,
               const double* x, const double* c, double* out) {
   ctx_t C;
@@ -678,11 +776,14 @@ int orc_brute(const double H[9], double r_img, int64_t N, const double* x, const
       if (s[3 * i + d] >= 1.0) s[3 * i + d] = 0.0;
     }
   }
+  window_t wd = make_window(0.25 * R, R);
   double* ei = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
   double* fi = (double*)calloc(3 * (size_t)(N > 0 ? N : 1), sizeof(double));
   double* wi = (double*)calloc(6 * (size_t)(N > 0 ? N : 1), sizeof(double));
 #pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
   for (int64_t i = 0; i < N; ++i) {
+    ksum_t ke = {0, 0}, kf[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum_t kw[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int64_t j = 0; j < N; ++j) {
       double ds[3] = {s[3 * j] - s[3 * i], s[3 * j + 1] - s[3 * i + 1], s[3 * j + 2] - s[3 * i + 2]};
       long lo[3], hi[3];
@@ -699,18 +800,26 @@ int orc_brute(const double H[9], double r_img, int64_t N, const double* x, const
             mv3(H, t, d3);
             double r2 = d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2];
             if (!(r2 < R * R)) continue;
-            double r6 = r2 * r2 * r2;
-            ei[i] += -0.5 * cc / r6;
-            double gp = -6.0 / (r6 * r2); /* (d/dr r^-6)/r */
-            for (int d = 0; d < 3; ++d) fi[3 * i + d] -= cc * gp * d3[d];
-            add_outer(wi + 6 * i, 0.5 * cc * gp, d3);
+            double r6 = r2 * r2 * r2, r = sqrt(r2), wv = win(&wd, r);
+            kadd(&ke, -0.5 * cc * wv / r6);
+            double gp = (-6.0 * wv / r + dwin(&wd, r)) / (r6 * r); /* (d/dr w r^-6)/r */
+            for (int d = 0; d < 3; ++d) kadd(&kf[d], -cc * gp * d3[d]);
+            kadd(&kw[0], 0.5 * cc * gp * d3[0] * d3[0]);
+            kadd(&kw[1], 0.5 * cc * gp * d3[1] * d3[1]);
+            kadd(&kw[2], 0.5 * cc * gp * d3[2] * d3[2]);
+            kadd(&kw[3], 0.5 * cc * gp * d3[0] * d3[1]);
+            kadd(&kw[4], 0.5 * cc * gp * d3[0] * d3[2]);
+            kadd(&kw[5], 0.5 * cc * gp * d3[1] * d3[2]);
           }
     }
+    ei[i] = kval(&ke);
+    for (int d = 0; d < 3; ++d) fi[3 * i + d] = kval(&kf[d]);
+    for (int d = 0; d < 6; ++d) wi[6 * i + d] = kval(&kw[d]);
   }
   double csum = 0.0;
   for (int64_t i = 0; i < N; ++i) csum += c[i];
-  double tailE = 4.0 * M_PI / (3.0 * R * R * R * vol);
-  double tailV = -8.0 * M_PI / (3.0 * R * R * R * vol);
+  double tailE = window_tail(&wd, vol);
+  double tailV = -tailE;
   double e = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t i = 0; i < N; ++i) {
     e += ei[i];

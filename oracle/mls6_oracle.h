@@ -49,8 +49,10 @@ int orc_grid_dims(const double L[3], double h, int levels, int n_out[3]);
  * Any output pointer may be NULL.  F: N*3, W: 6, eatom: N (per-atom energy
  * -1/2 c_i (e0_i + e_i) + 1/2 c_self c_i^2, which sums to E),
  * level_energy: levels+3 values as described above.
- * r_img: radius (absolute length) of the direct image sum for the coarsest
- * level table; <= 0 selects 64 * (largest cell-column length).
+ * r_img: outer radius (absolute length) of the windowed direct image sum of
+ * the coarsest-level table (window from 2^(l-1) a to r_img, complement
+ * integrated over space); <= 0 selects 2^(l-1) a + 21 V^(1/3), capped so
+ * that (coarsest points) x (images) stays near 3e7.
  * Returns 0 on success, <0 on bad arguments. */
 int orc_eval(const double H[9], double a, const int n[3], int levels, double r_img,
              int64_t N, const double* x, const double* c,
@@ -65,6 +67,12 @@ int orc_eval_sample(const double H[9], double a, const int n[3], int levels, dou
                     int64_t n_idx, const int64_t* idx,
                     double* F, double* eatom, double* grid_energy);
 
+/* Local part only (Eq. g_0) for the atoms listed in idx: e0 (n_idx) is
+ * sum_{j,n: r<a} c_j g_0(r) and F (n_idx*3) the local force.  Either output
+ * may be NULL. */
+int orc_local(const double H[9], double a, int64_t N, const double* x, const double* c,
+              int64_t n_idx, const int64_t* idx, double* e0, double* F);
+
 /* Stage export: writes, level after level, q^k, e^k and e^{k,tot} (each of
  * n_k points) for k = 1..levels into out (3 * sum_k n_k doubles). */
 int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img,
@@ -75,8 +83,11 @@ int orc_grids(const double H[9], double a, const int n[3], int levels, double r_
 int orc_top_table(const double H[9], double a, const int nl[3], int levels, double r_img,
                   double* T, double* V);
 
-/* Exact periodic sum by direct image summation out to radius r_img plus the
- * continuum tail.  Any output may be NULL.  F: N*3, W: 6. */
+/* Exact periodic sum sum_{j,n}' |x_j - x_i + H n|^-6 by windowed direct
+ * image summation (window from r_img/4 to r_img) plus the integral of the
+ * complement.  r_img >= 30 x (longest cell vector) keeps the aliasing error
+ * of the windowed split below ~1e-15 relative.  Any output may be NULL.
+ * F: N*3, W: 6. */
 int orc_brute(const double H[9], double r_img, int64_t N, const double* x, const double* c,
               double* E, double* F, double* W);
 

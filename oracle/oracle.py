@@ -56,6 +56,8 @@ def lib():
         L.orc_eval_sample.restype = C.c_int
         L.orc_eval_sample.argtypes = [_dp, C.c_double, _ip, C.c_int, C.c_double, C.c_int64, _dp,
                                       _dp, C.c_int64, _i64p, _dp, _dp, _dp]
+        L.orc_local.restype = C.c_int
+        L.orc_local.argtypes = [_dp, C.c_double, C.c_int64, _dp, _dp, C.c_int64, _i64p, _dp, _dp]
         L.orc_grids.restype = C.c_int
         L.orc_grids.argtypes = [_dp, C.c_double, _ip, C.c_int, C.c_double, C.c_int64, _dp, _dp, _dp]
         L.orc_top_table.restype = C.c_int
@@ -162,6 +164,20 @@ def evaluate_sample(box, a, n, levels, x, c, idx, r_img=0.0):
     if rc:
         raise ValueError(f"orc_eval_sample failed ({rc})")
     return dict(F=F, eatom=ea, grid_energy=float(eg[0]))
+
+
+def local(box, a, x, c, idx):
+    """Local part (Eq. g_0) for the atoms in idx: (e0, F)."""
+    H = _cell(box)
+    x, c = _atoms(x, c)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    e0 = np.zeros(idx.size)
+    F = np.zeros((idx.size, 3))
+    rc = lib().orc_local(_d(H), float(a), x.shape[0], _d(x), _d(c), idx.size,
+                         idx.ctypes.data_as(_i64p), _d(e0), _d(F))
+    if rc:
+        raise ValueError(f"orc_local failed ({rc})")
+    return e0, F
 
 
 def grids(box, a, n, levels, x, c, r_img=0.0):

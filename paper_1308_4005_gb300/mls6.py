@@ -1,0 +1,261 @@
+"""Thin ctypes binding of ``libmls6.so`` (see ``include/mls6.h``).
+
+The functions carry the C-ABI names and only marshal arguments; every step of
+an evaluation runs in the library's CUDA kernels.  Device buffers are passed
+as raw pointers (``tensor.data_ptr()``); PyTorch is used by callers only for
+device memory and streams.  If the library is missing or fails to load,
+``load()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmls6.so")
+
+MLS6_OK = 0
+MLS6_ERR_ARG = -1
+MLS6_ERR_GRID = -2
+MLS6_ERR_BOX = -3
+MLS6_ERR_ORDER = -4
+MLS6_ERR_CUDA = -5
+MLS6_ERR_NOMEM = -6
+MLS6_ERR_TIMEOUT = -7
+MLS6_ERR_NONFINITE = -8
+MLS6_ERR_SIZE = -9
+
+MLS6_FP64 = 0
+MLS6_FP32 = 1
+
+# every symbol declared in include/mls6.h
+EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream", "mls6_eval",
+           "mls6_eval_atoms", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
+           "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_destroy",
+           "mls6_status_string")
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class MLS6Error(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = status_string(code) if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+
+
+def load(path: str = LIB_PATH):
+    """Load the in-tree library (raises if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_1308_4005_gb300/build.py "
+                           "(the library has no CPU fallback)")
+    L = C.CDLL(path)
+    L.mls6_grid_dims.argtypes = [_dp, C.c_double, C.c_int, _ip]
+    L.mls6_grid_dims.restype = C.c_int
+    L.mls6_coarse_tables.argtypes = [_dp, _ip, C.c_int, C.c_double, _dp, _dp]
+    L.mls6_coarse_tables.restype = C.c_int
+    L.mls6_plan.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
+                            C.c_int, C.c_int, C.c_int]
+    L.mls6_plan.restype = C.c_int
+    L.mls6_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.mls6_set_stream.restype = C.c_int
+    L.mls6_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p]
+    L.mls6_eval.restype = C.c_int
+    L.mls6_eval_atoms.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]
+    L.mls6_eval_atoms.restype = C.c_int
+    L.mls6_last_error.argtypes = [C.c_void_p]
+    L.mls6_last_error.restype = C.c_int
+    L.mls6_plan_info.argtypes = [C.c_void_p, _ip, _dp, _ip, _ip]
+    L.mls6_plan_info.restype = C.c_int
+    L.mls6_debug_grid.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp]
+    L.mls6_debug_grid.restype = C.c_int
+    L.mls6_profile.argtypes = [C.c_void_p, C.c_int]
+    L.mls6_profile.restype = C.c_int
+    L.mls6_stage_times.argtypes = [C.c_void_p, _dp, C.c_int, _ip]
+    L.mls6_stage_times.restype = C.c_int
+    L.mls6_stage_name.argtypes = [C.c_int]
+    L.mls6_stage_name.restype = C.c_char_p
+    L.mls6_destroy.argtypes = [C.c_void_p]
+    L.mls6_destroy.restype = None
+    L.mls6_status_string.argtypes = [C.c_int]
+    L.mls6_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc, where):
+    if rc != MLS6_OK:
+        raise MLS6Error(rc, where)
+
+
+def _darr(vals):
+    return (C.c_double * len(vals))(*[float(v) for v in vals])
+
+
+def status_string(code: int) -> str:
+    return load().mls6_status_string(int(code)).decode()
+
+
+def mls6_grid_dims(box, h, levels):
+    n = (C.c_int * 3)()
+    _check(load().mls6_grid_dims(_darr(box), float(h), int(levels), n), "mls6_grid_dims")
+    return tuple(n)
+
+
+def mls6_coarse_tables(box, nl, levels, a):
+    import numpy as np
+
+    npk = int(nl[0]) * int(nl[1]) * int(nl[2])
+    T = np.zeros(npk)
+    V = np.zeros(6 * npk)
+    nn = (C.c_int * 3)(*[int(v) for v in nl])
+    _check(load().mls6_coarse_tables(_darr(box), nn, int(levels), float(a),
+                                     T.ctypes.data_as(_dp), V.ctypes.data_as(_dp)),
+           "mls6_coarse_tables")
+    return T, V.reshape(6, npk)
+
+
+def mls6_plan(box, N, a, h, levels, order=3, precision=MLS6_FP64):
+    """Returns an opaque plan handle (int)."""
+    out = C.c_void_p()
+    _check(load().mls6_plan(C.byref(out), _darr(box), int(N), float(a), float(h), int(levels),
+                            int(order), int(precision)), "mls6_plan")
+    return out.value
+
+
+def mls6_set_stream(plan, stream_handle):
+    _check(load().mls6_set_stream(C.c_void_p(plan), C.c_void_p(stream_handle or 0)),
+           "mls6_set_stream")
+
+
+def mls6_eval(plan, pos_ptr, c_ptr, forces_ptr, energy_ptr, virial_ptr):
+    """All pointers are integers (0 = NULL); energy/virial may be host or
+    device addresses."""
+    return load().mls6_eval(C.c_void_p(plan), C.c_void_p(pos_ptr or None),
+                            C.c_void_p(c_ptr or None), C.c_void_p(forces_ptr or None),
+                            C.c_void_p(energy_ptr or None), C.c_void_p(virial_ptr or None))
+
+
+def mls6_eval_atoms(plan, pos_ptr, c_ptr, forces_ptr, energy_ptr, virial_ptr, atom_energy_ptr):
+    return load().mls6_eval_atoms(C.c_void_p(plan), C.c_void_p(pos_ptr or None),
+                                  C.c_void_p(c_ptr or None), C.c_void_p(forces_ptr or None),
+                                  C.c_void_p(energy_ptr or None), C.c_void_p(virial_ptr or None),
+                                  C.c_void_p(atom_energy_ptr or None))
+
+
+def mls6_last_error(plan):
+    return load().mls6_last_error(C.c_void_p(plan))
+
+
+def mls6_plan_info(plan):
+    L = load()
+    lev = C.c_int()
+    nt = C.c_int()
+    _check(L.mls6_plan_info(C.c_void_p(plan), None, None, C.byref(lev), C.byref(nt)),
+           "mls6_plan_info")
+    ng = (C.c_int * (3 * lev.value))()
+    h = (C.c_double * 3)()
+    _check(L.mls6_plan_info(C.c_void_p(plan), ng, h, None, None), "mls6_plan_info")
+    dims = [tuple(ng[3 * k: 3 * k + 3]) for k in range(lev.value)]
+    return dict(levels=lev.value, n_grid=dims, h=tuple(h), ntaps=nt.value)
+
+
+def mls6_debug_grid(plan, level, which):
+    """Returns the grid as a numpy array shaped (nz, ny, nx)."""
+    import numpy as np
+
+    info = mls6_plan_info(plan)
+    n = info["n_grid"][level - 1]
+    out = np.zeros(n[0] * n[1] * n[2])
+    _check(load().mls6_debug_grid(C.c_void_p(plan), int(level), int(which),
+                                  out.ctypes.data_as(_dp)), "mls6_debug_grid")
+    return out.reshape(n[2], n[1], n[0])
+
+
+def mls6_profile(plan, enable=True):
+    _check(load().mls6_profile(C.c_void_p(plan), int(bool(enable))), "mls6_profile")
+
+
+def mls6_stage_times(plan):
+    """(dict stage -> ms of the last profiled evaluation, kernels launched)."""
+    ms = (C.c_double * 16)()
+    nl = C.c_int()
+    n = load().mls6_stage_times(C.c_void_p(plan), ms, 16, C.byref(nl))
+    if n < 0:
+        raise MLS6Error(n, "mls6_stage_times")
+    return {mls6_stage_name(i): ms[i] for i in range(n)}, nl.value
+
+
+def mls6_stage_name(i):
+    s = load().mls6_stage_name(int(i))
+    return s.decode() if s else None
+
+
+def mls6_destroy(plan):
+    if plan:
+        load().mls6_destroy(C.c_void_p(plan))
+
+
+class Plan:
+    """Owns one ``mls6_plan_t``; evaluates torch CUDA tensors in place.
+
+    ``evaluate(pos, c=None)`` takes a CUDA tensor of shape (N, 4) (x, y, z, c)
+    or (N, 3) plus c (N,), of the plan's dtype, and returns (E, F, W) with
+    F a new (N, 3) CUDA tensor.  Only marshalling happens here.
+    """
+
+    def __init__(self, box, N, a, h, levels, precision="fp64", order=3, stream=None):
+        self.precision = MLS6_FP64 if precision in ("fp64", MLS6_FP64) else MLS6_FP32
+        self.handle = mls6_plan(box, N, a, h, levels, order, self.precision)
+        self.N = int(N)
+        self.box = tuple(float(v) for v in box)
+        if stream is not None:
+            mls6_set_stream(self.handle, stream)
+
+    @property
+    def dtype(self):
+        import torch
+
+        return torch.float64 if self.precision == MLS6_FP64 else torch.float32
+
+    def info(self):
+        return mls6_plan_info(self.handle)
+
+    def evaluate(self, pos, c=None, virial=True, atom_energy=False, forces=None):
+        import torch
+
+        dev = pos.device
+        F = forces if forces is not None else torch.empty((self.N, 3), dtype=self.dtype,
+                                                          device=dev)
+        out = torch.zeros(7, dtype=torch.float64, device=dev)
+        ea = torch.empty(self.N, dtype=torch.float64, device=dev) if atom_energy else None
+        vp = out.data_ptr() + 8 if virial else 0
+        if ea is not None:
+            rc = mls6_eval_atoms(self.handle, pos.data_ptr(), c.data_ptr() if c is not None else 0,
+                                 F.data_ptr(), out.data_ptr(), vp, ea.data_ptr())
+        else:
+            rc = mls6_eval(self.handle, pos.data_ptr(), c.data_ptr() if c is not None else 0,
+                           F.data_ptr(), out.data_ptr(), vp)
+        _check(rc, "mls6_eval")
+        res = dict(out=out, F=F)
+        if ea is not None:
+            res["eatom"] = ea
+        return res
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mls6_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

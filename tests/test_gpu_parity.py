@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances
+  FP64 path (spec bar): |dE|/|E| <= 1e-12 and
+      max_i |F_i - F_i^orc| / RMS(F^orc) <= 1e-11; the virial and per-atom
+      energies are held to 1e-11 of their largest entry.
+  FP32 path (pair kernel and grids in float, energy/virial accumulated in
+      double): unit roundoff u = 2^-24 = 6.0e-8.  A force is a sum of ~100
+      pair terms of size up to ~30 (6 c^2 r^-7 at r = 0.8) that cancel to
+      O(1..10), plus a 64-node interpolation of grid potentials that are
+      themselves ~10^3-term stencil sums; the accumulated rounding is
+      bounded by ~ u * sqrt(terms) * max|term| ~ 6e-8 * 10 * 30 = 2e-5 of
+      the RMS force, and the tests use 1e-4.  Per-atom energies carry
+      u * sqrt(100) relative error and the total sums them in double, so
+      |dE|/|E| <= 2e-6.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+from paper_1308_4005_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = dict(E=1e-12, F=1e-11, W=1e-11, eatom=1e-11)
+TOL32 = dict(E=2e-6, F=1e-4, W=2e-5, eatom=2e-5)
+
+
+def gpu_eval(mls6, box, a, h, levels, x, c, prec, packed=True, virial=True, atom_energy=True,
+             shift=None):
+    import torch
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    N = len(c)
+    plan = mls6.Plan(box, N, a, h, levels, precision=prec)
+    xx = x if shift is None else x + shift
+    if packed:
+        pos = torch.tensor(np.c_[xx, c] if N else np.zeros((0, 4)), dtype=dt, device="cuda")
+        cc = None
+    else:
+        pos = torch.tensor(xx if N else np.zeros((0, 3)), dtype=dt, device="cuda").contiguous()
+        cc = torch.tensor(c, dtype=dt, device="cuda")
+    r = plan.evaluate(pos, cc, virial=virial, atom_energy=atom_energy)
+    torch.cuda.synchronize()
+    assert mls6.mls6_last_error(plan.handle) == 0
+    out = r["out"].cpu().numpy()
+    res = dict(E=out[0], W=out[1:7], F=r["F"].cpu().double().numpy(), plan=plan)
+    if atom_energy:
+        res["eatom"] = r["eatom"].cpu().numpy()
+    return res
+
+
+def as_prec(x, c, prec):
+    if prec == "fp32":
+        return x.astype(np.float32).astype(np.float64), c.astype(np.float32).astype(np.float64)
+    return x, c
+
+
+def compare(g, o, tol, label=""):
+    E_err = abs(g["E"] - o["E"]) / abs(o["E"])
+    rms = np.sqrt(np.mean(np.sum(o["F"] ** 2, axis=1)))
+    F_err = np.abs(g["F"] - o["F"]).max() / rms
+    W_err = np.abs(g["W"] - o["W"]).max() / np.abs(o["W"]).max()
+    msg = f"{label} dE={E_err:.3e} dF={F_err:.3e} dW={W_err:.3e}"
+    assert E_err <= tol["E"], msg
+    assert F_err <= tol["F"], msg
+    assert W_err <= tol["W"], msg
+    if "eatom" in g and "eatom" in o:
+        ea_err = np.abs(g["eatom"] - o["eatom"]).max() / np.abs(o["eatom"]).max()
+        assert ea_err <= tol["eatom"], f"{msg} deatom={ea_err:.3e}"
+    return E_err, F_err, W_err
+
+
+# ------------------------------------------------------------- FP64 parity
+
+def test_cube1000_fp64_parity(gpu_lib, orc):
+    """N=1000 cube, a=2.5, h=1 (-> 12^3, h=0.833), 3 levels, FP64."""
+    w = I.workload("cube1000")
+    x, c = I.generate(w)
+    n = orc.grid_dims(w.box, w.h, w.levels)
+    o = orc.evaluate(w.box, w.a, n, w.levels, x, c)
+    g = gpu_eval(gpu_lib, w.box, w.a, w.h, w.levels, x, c, "fp64")
+    compare(g, o, TOL64, "cube1000")
+    assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-13)
+
+
+def test_stage_grids_fp64(gpu_lib, orc):
+    """Every grid of every level: xi^k, e^k, e^{k,tot}."""
+    box, a, h, l = (8.0, 9.0, 10.0), 2.0, 0.5, 3
+    x, c = I.uniform_atoms(17, 300, box)
+    g = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64")
+    n = orc.grid_dims(box, h, l)
+    G = orc.grids(box, a, n, l, x, c)
+    for k in range(1, l + 1):
+        for which in range(3):
+            ref = G[k - 1][which]
+            got = gpu_lib.mls6_debug_grid(g["plan"].handle, k, which)
+            assert got.shape == ref.shape
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (k, which)
+
+
+CASES = [
+    # name, N, box, a, h, levels
+    ("one_atom", 1, (6.0, 6.0, 6.0), 2.0, 0.75, 2),
+    ("two_atoms", 2, (6.0, 7.0, 8.0), 2.0, 0.75, 2),
+    ("ragged_aniso", 37, (5.0, 6.0, 9.0), 1.8, 0.6, 3),
+    ("single_level", 300, (8.0, 8.0, 8.0), 2.0, 1.0, 1),
+    ("box_below_2a", 60, (4.0, 4.5, 5.0), 2.5, 0.5, 2),
+    ("tiny_top_grid", 200, (8.0, 8.0, 16.0), 1.5, 1.0, 4),
+    ("slab_5_levels", 900, (9.6, 9.6, 38.4), 2.4, 0.6, 5),
+    ("many_tiles", 3000, (16.0, 15.0, 14.0), 2.5, 0.7, 3),
+]
+
+
+@pytest.mark.parametrize("name,N,box,a,h,l", CASES, ids=[c[0] for c in CASES])
+def test_small_cases_fp64(gpu_lib, orc, name, N, box, a, h, l):
+    region = None
+    if name.startswith("slab"):
+        region = ((0, box[0]), (0, box[1]), (0.35 * box[2], 0.65 * box[2]))
+    x, c = I.uniform_atoms(zlib.crc32(name.encode()) % 10000, N, box, region=region)
+    n = orc.grid_dims(box, h, l)
+    o = orc.evaluate(box, a, n, l, x, c)
+    g = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64")
+    compare(g, o, TOL64, name)
+
+
+def test_no_atoms(gpu_lib):
+    g = gpu_eval(gpu_lib, (8.0, 8.0, 8.0), 2.0, 1.0, 3, np.zeros((0, 3)), np.zeros(0), "fp64")
+    assert g["E"] == 0.0
+    assert np.all(g["W"] == 0.0)
+
+
+def test_unwrapped_positions_and_separate_coefficients(gpu_lib, orc):
+    box, a, h, l = (7.0, 8.0, 9.0), 2.0, 0.7, 3
+    x, c = I.uniform_atoms(23, 200, box)
+    n = orc.grid_dims(box, h, l)
+    o = orc.evaluate(box, a, n, l, x, c)
+    k = np.random.default_rng(5).integers(-3, 4, size=x.shape)
+    g = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64", packed=False, shift=k * np.array(box))
+    compare(g, o, dict(E=1e-12, F=1e-10, W=1e-11, eatom=1e-11), "unwrapped")
+
+
+def test_repeatable_and_translation_by_coarsest_vector(gpu_lib):
+    box, a, h, l = (8.0, 8.0, 8.0), 2.0, 0.5, 3
+    x, c = I.uniform_atoms(29, 400, box)
+    g1 = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64")
+    g2 = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64")
+    assert g2["E"] == pytest.approx(g1["E"], rel=1e-14)
+    assert np.abs(g2["F"] - g1["F"]).max() <= 1e-13 * np.abs(g1["F"]).max()
+    s = np.array(box) / 16 * 4 * np.array([1, 2, 0])
+    g3 = gpu_eval(gpu_lib, box, a, h, l, x + s, c, "fp64")
+    assert g3["E"] == pytest.approx(g1["E"], rel=1e-12)
+    assert np.abs(g3["F"] - g1["F"]).max() <= 1e-11 * np.abs(g1["F"]).max()
+
+
+def test_nonfinite_input_is_reported(gpu_lib):
+    import torch
+
+    box = (8.0, 8.0, 8.0)
+    x, c = I.uniform_atoms(31, 50, box)
+    x[7, 1] = np.nan
+    plan = gpu_lib.Plan(box, 50, 2.0, 1.0, 2, precision="fp64")
+    pos = torch.tensor(np.c_[x, c], dtype=torch.float64, device="cuda")
+    F = torch.empty((50, 3), dtype=torch.float64, device="cuda")
+    import ctypes as C
+
+    E = C.c_double()
+    rc = gpu_lib.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), C.addressof(E), 0)
+    assert rc == gpu_lib.MLS6_ERR_NONFINITE
+    assert gpu_lib.mls6_last_error(plan.handle) == gpu_lib.MLS6_ERR_NONFINITE
+
+
+# ------------------------------------------------ FP32 and full-size parity
+
+def test_slab65536_fp32_parity(gpu_lib, orc):
+    """N=65,536 liquid/vacuum slab (40x40x120, rho=0.8), a=3, h=1.25, 4 levels,
+    FP32 with FP64 energy/virial: full comparison with the FP64 oracle."""
+    w = I.workload("slab65536")
+    x, c = I.generate(w)
+    x, c = as_prec(x, c, "fp32")
+    n = orc.grid_dims(w.box, w.h, w.levels)
+    o = orc.evaluate(w.box, w.a, n, w.levels, x, c)
+    g = gpu_eval(gpu_lib, w.box, w.a, w.h, w.levels, x, c, "fp32")
+    compare(g, o, TOL32, "slab65536/fp32")
+
+
+def test_slab65536_fp64_sampled(gpu_lib, orc):
+    w = I.workload("slab65536")
+    x, c = I.generate(w)
+    idx = np.random.default_rng(3).choice(w.N, 400, replace=False)
+    n = orc.grid_dims(w.box, w.h, w.levels)
+    o = orc.evaluate_sample(w.box, w.a, n, w.levels, x, c, idx)
+    g = gpu_eval(gpu_lib, w.box, w.a, w.h, w.levels, x, c, "fp64")
+    rms = np.sqrt(np.mean(np.sum(g["F"] ** 2, axis=1)))
+    assert np.abs(g["F"][idx] - o["F"]).max() <= 1e-11 * rms
+    assert np.abs(g["eatom"][idx] - o["eatom"]).max() <= 1e-11 * np.abs(o["eatom"]).max()
+    assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-13)
+
+
+@pytest.mark.slow
+def test_cube1m_fp32_sampled(gpu_lib, orc):
+    """N=1,048,576 cube at rho=0.85, a=3, h=1 (112^3), 5 levels, FP32: sampled
+    atoms against the oracle (forces and per-atom energies), the total as the
+    double sum of per-atom energies."""
+    w = I.workload("cube1m")
+    x, c = I.generate(w)
+    x, c = as_prec(x, c, "fp32")
+    idx = np.random.default_rng(4).choice(w.N, 300, replace=False)
+    n = orc.grid_dims(w.box, w.h, w.levels)
+    o = orc.evaluate_sample(w.box, w.a, n, w.levels, x, c, idx)
+    g = gpu_eval(gpu_lib, w.box, w.a, w.h, w.levels, x, c, "fp32")
+    rms = np.sqrt(np.mean(np.sum(g["F"] ** 2, axis=1)))
+    assert np.abs(g["F"][idx] - o["F"]).max() <= TOL32["F"] * rms
+    assert np.abs(g["eatom"][idx] - o["eatom"]).max() <= TOL32["eatom"] * np.abs(o["eatom"]).max()
+    assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-12)
