@@ -91,8 +91,18 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
               int order, int precision);
 
 /* Enqueue subsequent work of the plan on a cudaStream_t (NULL = legacy
- * default stream). */
+ * default stream).  Internally an evaluation runs on two streams owned by
+ * the plan (the pair sum in parallel with the grid chain); they wait for
+ * the caller's stream at the start and the caller's stream waits for them
+ * at the end, so ordering is as if all work ran on the caller's stream. */
 int mls6_set_stream(mls6_plan_t* p, void* stream);
+
+/* Graph execution (default on): the first evaluation with a given set of
+ * pointers and options captures the whole kernel sequence into a CUDA
+ * graph, later evaluations with the same pointers replay it (re-captured
+ * when pointers, virial or profiling change).  enable = 0 launches the
+ * kernels one by one. */
+int mls6_set_graph(mls6_plan_t* p, int enable);
 
 /* Evaluate energy, forces and virial.
  *   pos     device pointer, N rows of the plan's precision (double or float):
@@ -133,8 +143,10 @@ int mls6_plan_info(const mls6_plan_t* p, int* n_grid, double* h_actual, int* lev
  * level: 1..l.  Synchronises the plan's stream. */
 int mls6_debug_grid(mls6_plan_t* p, int level, int which, double* host_out);
 
-/* Per-stage timing with CUDA events on the plan's stream (off by default).
- * While enabled, every evaluation records an event at each stage boundary:
+/* Per-stage timing with CUDA events (off by default).  While enabled, the
+ * evaluation runs its stages one after another on one stream (the pair
+ * sum no longer overlaps the grid chain) and records an event at the start
+ * and end of each stage:
  * 0 bin (wrap, cell histogram, scan, scatter, per-cell order), 1 pair
  * (local part), 2 anterpolation, 3 restriction, 4 level stencils,
  * 5 coarsest level, 6 prolongation, 7 interpolation/forces, 8 reduction. */

@@ -1,0 +1,176 @@
+// Spatial binning of the atoms (the linked-cell structure of Sec. III.D):
+// wrap positions into the box, histogram them over cells of width >= a/2,
+// exclusive scan of the counts, scatter into cell order, and order each
+// cell by input index so that every later sum runs in a reproducible order.
+#include "mls6_device.cuh"
+
+namespace mls6 {
+
+static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
+
+template <typename T> struct BinArgs {
+  Box3<T> box;
+  T inv_w[3];
+  int nc[3];
+};
+
+template <typename T>
+__global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
+                      BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
+                      int* __restrict__ count, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const T* p = pos + (size_t)i * stride;
+  T x = p[0], y = p[1], z = p[2];
+  T c = cc ? cc[i] : p[3];
+  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(c))) {
+    atomicOr(flag, 1);
+    x = y = z = c = T(0);
+  }
+  x = wrapx(x, g.box.L[0], g.box.invL[0]);
+  y = wrapx(y, g.box.L[1], g.box.invL[1]);
+  z = wrapx(z, g.box.L[2], g.box.invL[2]);
+  int cx = min(max((int)(x * g.inv_w[0]), 0), g.nc[0] - 1);
+  int cy = min(max((int)(y * g.inv_w[1]), 0), g.nc[1] - 1);
+  int cz = min(max((int)(z * g.inv_w[2]), 0), g.nc[2] - 1);
+  int cell = cx + g.nc[0] * (cy + g.nc[1] * cz);
+  cell_of[i] = cell;
+  Vec4<T> v;
+  v.x = x;
+  v.y = y;
+  v.z = z;
+  v.w = c;
+  posw[i] = v;
+  atomicAdd(&count[cell], 1);
+}
+
+// Phase 1: per-tile sums of the cell counts.
+__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum) {
+  __shared__ double sh[32];
+  long base = (long)blockIdx.x * kScanTile;
+  int s = 0;
+  for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
+    if (base + t < n) s += count[base + t];
+  double tot = block_sum((double)s, sh);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = (int)tot;
+}
+
+// Phase 2: exclusive scan of the (few hundred) tile sums in one thread;
+// writes the grand total to start[n].
+__global__ void k_scan_top(int* __restrict__ tsum, int ntiles, int* __restrict__ start, long n) {
+  if (threadIdx.x != 0) return;
+  int acc = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    int v = tsum[t];
+    tsum[t] = acc;
+    acc += v;
+  }
+  start[n] = acc;
+}
+
+// Phase 3: scan inside each tile (256 threads x 8 consecutive cells), write
+// start[], reset count[] for use as fill counters by the scatter.
+__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ toff,
+                             int* __restrict__ start) {
+  __shared__ int wsum[32];
+  constexpr int PER = kScanTile / 256;
+  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * PER;
+  int v[PER], s = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    v[k] = (base + k < n) ? count[base + k] : 0;
+    s += v[k];
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  int excl = incl - s + (wid > 0 ? wsum[wid - 1] : 0) + toff[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    if (base + k < n) {
+      start[base + k] = excl;
+      count[base + k] = 0;
+    }
+    excl += v[k];
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
+                          const int* __restrict__ start, int* __restrict__ fill,
+                          Vec4<T>* __restrict__ sorted, int* __restrict__ sidx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int cell = cell_of[i];
+  int slot = start[cell] + atomicAdd(&fill[cell], 1);
+  sorted[slot] = posw[i];
+  sidx[slot] = i;
+}
+
+// Insertion sort of each cell by input index (cells above 256 atoms are
+// left in scatter order: results stay correct, only bitwise
+// reproducibility is lost for them).
+template <typename T>
+__global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
+                           int* __restrict__ sidx) {
+  long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= ncell) return;
+  int b = start[cell], e = start[cell + 1];
+  if (e - b < 2 || e - b > 256) return;
+  for (int i = b + 1; i < e; ++i) {
+    int key = sidx[i];
+    Vec4<T> v = sorted[i];
+    int j = i - 1;
+    while (j >= b && sidx[j] > key) {
+      sidx[j + 1] = sidx[j];
+      sorted[j + 1] = sorted[j];
+      --j;
+    }
+    sidx[j + 1] = key;
+    sorted[j + 1] = v;
+  }
+}
+
+template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStream_t st) {
+  const int N = (int)p->N;
+  BinArgs<T> bg;
+  for (int d = 0; d < 3; ++d) {
+    bg.box.L[d] = (T)p->L[d];
+    bg.box.invL[d] = (T)(1.0 / p->L[d]);
+    bg.inv_w[d] = (T)p->cg.inv_w[d];
+    bg.nc[d] = p->cg.nc[d];
+  }
+  const long ncell = p->cg.ncell;
+  const long ntiles = cdiv(ncell, kScanTile);
+  cudaMemsetAsync(p->d_cell_count, 0, sizeof(int) * ncell, st);
+  k_bin<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
+                                              p->d_cell_of, p->d_cell_count, p->d_flag);
+  k_scan_tiles<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan);
+  k_scan_top<<<1, 32, 0, st>>>(p->d_scan, (int)ntiles, p->d_cell_start, ncell);
+  k_scan_final<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
+  k_scatter<T><<<cdiv(N, kBlock), kBlock, 0, st>>>((const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
+                                                  p->d_cell_start, p->d_cell_count,
+                                                  (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
+  k_cellsort<T><<<cdiv(ncell, kBlock), kBlock, 0, st>>>(p->d_cell_start, ncell,
+                                                       (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
+  return 6;
+}
+
+template int launch_bin<float>(Plan*, const float*, const float*, cudaStream_t);
+template int launch_bin<double>(Plan*, const double*, const double*, cudaStream_t);
+
+}  // namespace mls6

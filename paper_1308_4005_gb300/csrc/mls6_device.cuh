@@ -1,0 +1,79 @@
+// Device helpers shared by the kernels of the multilevel summation library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mls6_internal.h"
+
+namespace mls6 {
+
+template <typename T> struct Box3 {
+  T L[3], invL[3];
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  int m = i % n;
+  return m < 0 ? m + n : m;
+}
+
+// Position wrapped into [0, L).
+template <typename T> __device__ __forceinline__ T wrapx(T x, T L, T invL) {
+  T r = x - floor(x * invL) * L;
+  if (r < T(0)) r += L;
+  if (r >= L) r -= L;
+  if (!(r >= T(0) && r < L)) r = T(0);
+  return r;
+}
+
+// Weights of the four nodes base-1 .. base+2 of Eq. (Phi-Hermite) for an
+// atom at fractional offset t in [0,1) from node base -- Phi(1+t), Phi(t),
+// Phi(1-t), Phi(2-t) -- and (phi4 only) their derivatives in t.
+template <typename T> __device__ __forceinline__ void phi4w(T t, T w[4]) {
+  T s = T(1) - t;
+  w[0] = T(-0.5) * t * s * s;
+  w[1] = s * (T(1) + t - T(1.5) * t * t);
+  w[2] = t * (T(1) + s - T(1.5) * s * s);
+  w[3] = T(-0.5) * s * t * t;
+}
+
+template <typename T> __device__ __forceinline__ void phi4(T t, T w[4], T dw[4]) {
+  phi4w(t, w);
+  T s = T(1) - t;
+  dw[0] = T(-0.5) * s * (T(1) - T(3) * t);
+  dw[1] = t * (T(-5) + T(4.5) * t);
+  dw[2] = s * (T(5) - T(4.5) * s);
+  dw[3] = T(-0.5) * t * (T(2) - T(3) * t);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sums of NV doubles (blockDim.x a multiple of 32, <= 1024);
+// results valid in thread 0; fixed reduction order.  sh: >= 32*NV doubles.
+template <int NV> __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) v[c] = warp_sum(v[c]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sh[c * 32 + wid] = v[c];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[c * 32 + w];
+      v[c] = s;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  double a[1] = {v};
+  block_sum_n<1>(a, sh);
+  return a[0];
+}
+
+}  // namespace mls6

@@ -1,0 +1,686 @@
+// Grid part of multilevel summation (Sec. II.B): anterpolation, restriction,
+// evaluation on every level, prolongation and interpolation.
+#include <cmath>
+
+#include "mls6_device.cuh"
+
+namespace mls6 {
+
+static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------ anterpolation
+
+// Eq. (anterpolation): q^1_mu += c_j phi_mu(x_j) over the 4x4x4 nodes of
+// every atom (sorted order keeps the atomics of a warp in few cache lines).
+template <typename T>
+__global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0,
+                         T ih1, T ih2, T* __restrict__ q) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  Vec4<T> p = sp[i];
+  T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
+  T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
+  int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
+  T wx[4], wy[4], wz[4];
+  phi4w(u0 - f0, wx);
+  phi4w(u1 - f1, wy);
+  phi4w(u2 - f2, wz);
+  int ix[4], iy[4], iz[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ix[k] = wrapi(b0 - 1 + k, n0);
+    iy[k] = wrapi(b1 - 1 + k, n1);
+    iz[k] = wrapi(b2 - 1 + k, n2);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      T wyz = p.w * wy[b] * wz[c];
+      long rowi = (long)n0 * (iy[b] + (long)n1 * iz[c]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) atomicAdd(&q[rowi + ix[a]], wyz * wx[a]);
+    }
+}
+
+// Brick-tiled anterpolation: one block per kAB^3 brick of finest nodes.  The
+// block walks the cells covering the brick's influence region (atoms whose
+// 4-node support meets the brick, with periodic images as shifts of whole
+// boxes), accumulates their weights into the brick in shared memory and
+// stores the brick once: no global atomics.  Node assignment (base node and
+// fractional offset) is computed from the wrapped position exactly as in
+// the interpolation, so both see the same basis functions.
+constexpr int kAB = 8;
+constexpr int kAnterpThreads = 256;
+constexpr int kAnterpMaxCells = 16;  // cells per axis of an influence region
+
+template <typename T> struct AnterpArgs {
+  int n[3];
+  T ih[3];
+  T h[3];
+  int nc[3];
+  T inv_w[3];
+  int bricks[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kAnterpThreads) k_anterp_tiled(
+    const Vec4<T>* __restrict__ sp, const int* __restrict__ start, AnterpArgs<T> A,
+    T* __restrict__ q) {
+  __shared__ int cst[kAnterpMaxCells * kAnterpMaxCells * kAnterpMaxCells + 1];
+  __shared__ int cmeta[3][2];  // per axis: first unwrapped cell, count
+  __shared__ T acc[kAB * kAB * kAB];
+  __shared__ int s_tot;
+  const int b = blockIdx.x;
+  const int bx = b % A.bricks[0], by = (b / A.bricks[0]) % A.bricks[1],
+            bz = b / (A.bricks[0] * A.bricks[1]);
+  const int lo[3] = {bx * kAB, by * kAB, bz * kAB};
+  for (int i = threadIdx.x; i < kAB * kAB * kAB; i += blockDim.x) acc[i] = T(0);
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
+    // influence region in space: u in [lo-2, lo+kAB+1) nodes
+    T x0 = (T)(lo[d] - 2) * A.h[d], x1 = (T)(lo[d] + kAB + 1) * A.h[d];
+    int c0 = (int)floor(x0 * A.inv_w[d]) - 1, c1 = (int)floor(x1 * A.inv_w[d]) + 1;
+    cmeta[d][0] = c0;
+    cmeta[d][1] = c1 - c0 + 1;
+  }
+  __syncthreads();
+  const int m0 = cmeta[0][1], m1 = cmeta[1][1], m2 = cmeta[2][1];
+  const int ncells = m0 * m1 * m2;
+  for (int c = threadIdx.x; c < ncells; c += blockDim.x) {
+    int ux = cmeta[0][0] + c % m0, uy = cmeta[1][0] + (c / m0) % m1,
+        uz = cmeta[2][0] + c / (m0 * m1);
+    int gc = wrapi(ux, A.nc[0]) + A.nc[0] * (wrapi(uy, A.nc[1]) + A.nc[1] * wrapi(uz, A.nc[2]));
+    cst[c + 1] = start[gc + 1] - start[gc];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int base = 0; base < ncells; base += 32) {
+      int c = base + threadIdx.x;
+      int v = c < ncells ? cst[c + 1] : 0;
+      int incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (threadIdx.x >= o) incl += u;
+      }
+      if (c < ncells) cst[c + 1] = carry + incl;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (threadIdx.x == 0) {
+      cst[0] = 0;
+      s_tot = carry;
+    }
+  }
+  __syncthreads();
+  const int tot = s_tot;
+  for (int s = threadIdx.x; s < tot; s += blockDim.x) {
+    int lo_c = 0, hi_c = ncells;  // cst[lo_c] <= s < cst[hi_c]
+    while (hi_c - lo_c > 1) {
+      int mid = (lo_c + hi_c) >> 1;
+      if (cst[mid] <= s) lo_c = mid; else hi_c = mid;
+    }
+    const int c = lo_c;
+    const int u[3] = {cmeta[0][0] + c % m0, cmeta[1][0] + (c / m0) % m1,
+                      cmeta[2][0] + c / (m0 * m1)};
+    int g[3], shift[3];
+    for (int d = 0; d < 3; ++d) {
+      g[d] = wrapi(u[d], A.nc[d]);
+      shift[d] = (u[d] - g[d]) / A.nc[d];  // whole boxes
+    }
+    const int gc = g[0] + A.nc[0] * (g[1] + A.nc[1] * g[2]);
+    const Vec4<T> p = sp[start[gc] + (s - cst[c])];
+    const T pos[3] = {p.x, p.y, p.z};
+    T w[3][4];
+    int first[3];  // brick-relative index of the first support node
+    bool any = true;
+    for (int d = 0; d < 3; ++d) {
+      T ud = pos[d] * A.ih[d];
+      T fd = floor(ud);
+      phi4w(ud - fd, w[d]);
+      first[d] = (int)fd - 1 + shift[d] * A.n[d] - lo[d];
+      any = any && (first[d] < kAB) && (first[d] + 3 >= 0);
+    }
+    if (!any) continue;
+    for (int kz = 0; kz < 4; ++kz) {
+      const int z = first[2] + kz;
+      if (z < 0 || z >= kAB) continue;
+      for (int ky = 0; ky < 4; ++ky) {
+        const int y = first[1] + ky;
+        if (y < 0 || y >= kAB) continue;
+        const T wyz = p.w * w[1][ky] * w[2][kz];
+        for (int kx = 0; kx < 4; ++kx) {
+          const int x = first[0] + kx;
+          if (x < 0 || x >= kAB) continue;
+          atomicAdd(&acc[x + kAB * (y + kAB * z)], wyz * w[0][kx]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kAB * kAB * kAB; i += blockDim.x) {
+    const int x = lo[0] + i % kAB, y = lo[1] + (i / kAB) % kAB, z = lo[2] + i / (kAB * kAB);
+    if (x < A.n[0] && y < A.n[1] && z < A.n[2])
+      q[x + (long)A.n[0] * (y + (long)A.n[1] * z)] = acc[i];
+  }
+}
+
+// Cells per axis of an influence region; 0 if the tiled kernel cannot be
+// used (then the per-atom atomic kernel runs).
+static int anterp_region_cells(const Plan* p) {
+  int mx = 0;
+  for (int d = 0; d < 3; ++d) {
+    double span = (kAB + 3) * p->lv[1].h[d] * p->cg.inv_w[d];
+    int m = (int)std::ceil(span) + 3;
+    mx = std::max(mx, m);
+  }
+  return mx <= kAnterpMaxCells ? mx : 0;
+}
+
+template <typename T> int launch_anterp(Plan* p, cudaStream_t st) {
+  const Level& L1 = p->lv[1];
+  const int N = (int)p->N;
+  if (anterp_region_cells(p) > 0) {
+    AnterpArgs<T> A;
+    long nb = 1;
+    for (int d = 0; d < 3; ++d) {
+      A.n[d] = L1.n[d];
+      A.ih[d] = (T)(1.0 / L1.h[d]);
+      A.h[d] = (T)L1.h[d];
+      A.nc[d] = p->cg.nc[d];
+      A.inv_w[d] = (T)p->cg.inv_w[d];
+      A.bricks[d] = (int)cdiv(L1.n[d], kAB);
+      nb *= A.bricks[d];
+    }
+    k_anterp_tiled<T><<<nb, kAnterpThreads, 0, st>>>((const Vec4<T>*)p->d_sorted,
+                                                     p->d_cell_start, A, (T*)p->d_q[1]);
+    return 1;
+  }
+  k_anterp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+      (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
+      (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (T*)p->d_q[1]);
+  return 1;
+}
+
+// -------------------------------------------------------------- restriction
+
+// q^{k+1}_mu = sum_nu prod_d Phi(nu_d/2 - mu_d) q^k_nu; the nonzero weights
+// are Phi(0)=1, Phi(1/2)=9/16, Phi(3/2)=-1/16 at fine offsets 0, +-1, +-3
+// from 2 mu.
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
+                           int c0, int c1, int c2) {
+  long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long np = (long)c0 * c1 * c2;
+  if (mu >= np) return;
+  int m0 = (int)(mu % c0), m1 = (int)((mu / c0) % c1), m2 = (int)(mu / ((long)c0 * c1));
+  const int off[5] = {-3, -1, 0, 1, 3};
+  const T wt[5] = {T(-0.0625), T(0.5625), T(1), T(0.5625), T(-0.0625)};
+  T acc = 0;
+  for (int c = 0; c < 5; ++c) {
+    int z = wrapi(2 * m2 + off[c], f2);
+    for (int b = 0; b < 5; ++b) {
+      int y = wrapi(2 * m1 + off[b], f1);
+      long row = (long)f0 * (y + (long)f1 * z);
+      T wyz = wt[b] * wt[c];
+      T s = 0;
+      for (int a = 0; a < 5; ++a) s += wt[a] * qf[row + wrapi(2 * m0 + off[a], f0)];
+      acc += wyz * s;
+    }
+  }
+  qc[mu] = acc;
+}
+
+template <typename T> int launch_restrict(Plan* p, int k, cudaStream_t st) {
+  const Level &F = p->lv[k], &C = p->lv[k + 1];
+  k_restrict<T><<<cdiv(C.np, kBlock), kBlock, 0, st>>>((const T*)p->d_q[k], F.n[0], F.n[1],
+                                                      F.n[2], (T*)p->d_q[k + 1], C.n[0], C.n[1],
+                                                      C.n[2]);
+  return 1;
+}
+
+// ------------------------------------------------------- level stencils
+
+template <typename T> struct StencilLevel {
+  const T* q;
+  T* e;
+  int n[3];
+  int tiles[3];
+  long tile_off;
+  T scale;  // 2^(-6(k-1))
+};
+
+template <typename T> struct StencilArgs {
+  StencilLevel<T> lv[kMaxLevels];
+  int nlev, P, S, nrows, ntaps;
+  const int4* rows;     // dy, dz, R, first tap
+  const Vec4<T>* wv;    // g_1, G, G dx, G dx^2 per tap
+  double hc[6];         // h_x^2, h_y^2, h_z^2, h_x h_y, h_x h_z, h_y h_z (level 1)
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Eq. (evaluation) on all levels k < l in one launch.  Block = one 8x8x8
+// output tile of one level; the tile plus a halo of P nodes (periodic) is
+// staged in shared memory together with the tap table.  Each thread owns
+// 4 consecutive x nodes and slides a 4-wide register window along every tap
+// row (constant dy, dz).  The strain derivative is accumulated per row from
+// three row sums of the node/neighbour products (taps G, G dx, G dx^2), so
+// the six virial components cost 7 FMAs per tap and thread instead of 24.
+template <typename T, bool VIR>
+__global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<T> A,
+                                                             double* __restrict__ wpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32 * 6];
+  const int S = A.S, P = A.P, S2 = S * S, S3 = S2 * S;
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  Vec4<T>* wv = reinterpret_cast<Vec4<T>*>(smem_raw + align16(sizeof(T) * S3));
+  int4* rows = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(wv) +
+                                       sizeof(Vec4<T>) * A.ntaps);
+  const long b = blockIdx.x;
+  int k = 0;
+  while (k + 1 < A.nlev && b >= A.lv[k + 1].tile_off) ++k;
+  const T* __restrict__ q = A.lv[k].q;
+  const int n0 = A.lv[k].n[0], n1 = A.lv[k].n[1], n2 = A.lv[k].n[2];
+  const long t = b - A.lv[k].tile_off;
+  const int tx = (int)(t % A.lv[k].tiles[0]);
+  const int ty = (int)((t / A.lv[k].tiles[0]) % A.lv[k].tiles[1]);
+  const int tz = (int)(t / ((long)A.lv[k].tiles[0] * A.lv[k].tiles[1]));
+  const int ox = tx * kStencilTile, oy = ty * kStencilTile, oz = tz * kStencilTile;
+
+  for (int i = threadIdx.x; i < A.ntaps; i += blockDim.x) wv[i] = A.wv[i];
+  for (int i = threadIdx.x; i < A.nrows; i += blockDim.x) rows[i] = A.rows[i];
+  for (int i = threadIdx.x; i < S3; i += blockDim.x) {
+    int ix = i % S, iy = (i / S) % S, iz = i / S2;
+    int gx = wrapi(ox + ix - P, n0), gy = wrapi(oy + iy - P, n1), gz = wrapi(oz + iz - P, n2);
+    tile[i] = q[gx + (long)n0 * (gy + (long)n1 * gz)];
+  }
+  __syncthreads();
+
+  const int lx = (threadIdx.x & 1) * kStencilW, ly = (threadIdx.x >> 1) & 7,
+            lz = threadIdx.x >> 4;
+  const bool row_in = (oy + ly < n1) && (oz + lz < n2);
+  T qv[kStencilW];
+#pragma unroll
+  for (int w = 0; w < kStencilW; ++w)
+    qv[w] = (row_in && ox + lx + w < n0) ? tile[(lz + P) * S2 + (ly + P) * S + lx + P + w] : T(0);
+  T acc[kStencilW];
+#pragma unroll
+  for (int w = 0; w < kStencilW; ++w) acc[w] = T(0);
+  T vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0;
+  for (int r = 0; r < A.nrows; ++r) {
+    const int4 ri = rows[r];
+    const T* in = tile + (lz + P + ri.y) * S2 + (ly + P + ri.x) * S + (lx + P - ri.z);
+    const Vec4<T>* ww = wv + ri.w;
+    const int nd = 2 * ri.z + 1;
+    T b0 = in[0], b1 = in[1], b2 = in[2];
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int d = 0; d < nd; ++d) {
+      const T b3 = in[d + 3];
+      const Vec4<T> wt = ww[d];
+      acc[0] += wt.x * b0;
+      acc[1] += wt.x * b1;
+      acc[2] += wt.x * b2;
+      acc[3] += wt.x * b3;
+      if (VIR) {
+        const T cd = qv[0] * b0 + qv[1] * b1 + qv[2] * b2 + qv[3] * b3;
+        s0 += wt.y * cd;
+        s1 += wt.z * cd;
+        s2 += wt.w * cd;
+      }
+      b0 = b1;
+      b1 = b2;
+      b2 = b3;
+    }
+    if (VIR) {
+      const T dy = (T)ri.x, dz = (T)ri.y;
+      vxx += s2;
+      vyy += dy * dy * s0;
+      vzz += dz * dz * s0;
+      vxy += dy * s1;
+      vxz += dz * s1;
+      vyz += dy * dz * s0;
+    }
+  }
+  const T scale = A.lv[k].scale;
+  if (row_in) {
+    T* e = A.lv[k].e + (ox + lx) + (long)n0 * ((oy + ly) + (long)n1 * (oz + lz));
+#pragma unroll
+    for (int w = 0; w < kStencilW; ++w)
+      if (ox + lx + w < n0) e[w] = scale * acc[w];
+  }
+  if (VIR) {
+    const double hs = 0.5 * (double)scale;
+    double v6[6] = {hs * A.hc[0] * (double)vxx, hs * A.hc[1] * (double)vyy,
+                    hs * A.hc[2] * (double)vzz, hs * A.hc[3] * (double)vxy,
+                    hs * A.hc[4] * (double)vxz, hs * A.hc[5] * (double)vyz};
+    block_sum_n<6>(v6, red);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) wpart[6 * b + c] = v6[c];
+  }
+}
+
+// Same evaluation without shared-memory staging, for stencils whose tile
+// and tap table exceed the shared-memory budget (large 2a/h): one thread per
+// node, periodic indices, taps read from global memory (warp-uniform).
+template <typename T, bool VIR>
+__global__ void __launch_bounds__(kBlock) k_stencil_global(StencilArgs<T> A,
+                                                           double* __restrict__ wpart,
+                                                           long nodes_total) {
+  __shared__ double red[32 * 6];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  // level of this node (levels are concatenated)
+  long off = 0;
+  int k = 0;
+  for (; k < A.nlev; ++k) {
+    long np = (long)A.lv[k].n[0] * A.lv[k].n[1] * A.lv[k].n[2];
+    if (gid < off + np) break;
+    off += np;
+  }
+  T acc = 0, vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0, qmu = 0;
+  T scale = 0;
+  if (gid < nodes_total) {
+    const T* __restrict__ q = A.lv[k].q;
+    const int n0 = A.lv[k].n[0], n1 = A.lv[k].n[1], n2 = A.lv[k].n[2];
+    const long mu = gid - off;
+    const int x = (int)(mu % n0), y = (int)((mu / n0) % n1), z = (int)(mu / ((long)n0 * n1));
+    qmu = q[mu];
+    for (int r = 0; r < A.nrows; ++r) {
+      const int4 ri = A.rows[r];
+      const long rowb = (long)n0 * (wrapi(y + ri.x, n1) + (long)n1 * wrapi(z + ri.y, n2));
+      T s0 = 0, s1 = 0, s2 = 0;
+      for (int d = 0; d <= 2 * ri.z; ++d) {
+        const T v = q[rowb + wrapi(x + d - ri.z, n0)];
+        const Vec4<T> wt = A.wv[ri.w + d];
+        acc += wt.x * v;
+        if (VIR) {
+          s0 += wt.y * v;
+          s1 += wt.z * v;
+          s2 += wt.w * v;
+        }
+      }
+      if (VIR) {
+        const T dy = (T)ri.x, dz = (T)ri.y;
+        vxx += qmu * s2;
+        vyy += qmu * dy * dy * s0;
+        vzz += qmu * dz * dz * s0;
+        vxy += qmu * dy * s1;
+        vxz += qmu * dz * s1;
+        vyz += qmu * dy * dz * s0;
+      }
+    }
+    scale = A.lv[k].scale;
+    A.lv[k].e[mu] = scale * acc;
+  }
+  if (VIR) {
+    const double hs = 0.5 * (double)scale;
+    double v6[6] = {hs * A.hc[0] * (double)vxx, hs * A.hc[1] * (double)vyy,
+                    hs * A.hc[2] * (double)vzz, hs * A.hc[3] * (double)vxy,
+                    hs * A.hc[4] * (double)vxz, hs * A.hc[5] * (double)vyz};
+    block_sum_n<6>(v6, red);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = v6[c];
+  }
+}
+
+template <typename T> static StencilArgs<T> stencil_args(Plan* p) {
+  StencilArgs<T> A;
+  A.nlev = p->levels - 1;
+  A.P = p->P;
+  A.S = kStencilTile + 2 * p->P;
+  A.nrows = p->nrows;
+  A.ntaps = p->ntaps;
+  A.rows = reinterpret_cast<const int4*>(p->d_rows);
+  A.wv = reinterpret_cast<const Vec4<T>*>(p->d_wv);
+  const double* h = p->lv[1].h;
+  A.hc[0] = h[0] * h[0];
+  A.hc[1] = h[1] * h[1];
+  A.hc[2] = h[2] * h[2];
+  A.hc[3] = h[0] * h[1];
+  A.hc[4] = h[0] * h[2];
+  A.hc[5] = h[1] * h[2];
+  for (int k = 1; k < p->levels; ++k) {
+    StencilLevel<T>& L = A.lv[k - 1];
+    L.q = (const T*)p->d_q[k];
+    L.e = (T*)p->d_e[k];
+    for (int d = 0; d < 3; ++d) {
+      L.n[d] = p->lv[k].n[d];
+      L.tiles[d] = p->tiles[k][d];
+    }
+    L.tile_off = p->tile_off[k];
+    L.scale = (T)std::ldexp(1.0, -6 * (k - 1));
+  }
+  return A;
+}
+
+template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
+  if (p->levels < 2) return 0;
+  StencilArgs<T> A = stencil_args<T>(p);
+  double* wp = p->d_wpart + 6 * p->wpart_stencil;
+  if (p->stencil_global) {
+    long nodes = 0;
+    for (int k = 1; k < p->levels; ++k) nodes += p->lv[k].np;
+    if (vir)
+      k_stencil_global<T, true><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
+    else
+      k_stencil_global<T, false><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
+    return 1;
+  }
+  if (vir)
+    k_stencil<T, true><<<p->stencil_blocks, kStencilThreads, p->stencil_smem, st>>>(A, wp);
+  else
+    k_stencil<T, false><<<p->stencil_blocks, kStencilThreads, p->stencil_smem, st>>>(A, wp);
+  return 1;
+}
+
+// ------------------------------------------------------------ coarsest level
+
+// Eq. (last-grid-periodic-transformed) in FP64: one block per coarsest node
+// mu, threads stride over nu, e_mu = sum_nu T[(mu - nu) mod n] q_nu; the
+// virial adds 1/2 q_mu sum_nu V[(mu - nu) mod n] q_nu.
+template <typename T, bool VIR>
+__global__ void __launch_bounds__(128) k_top(const T* __restrict__ q, int n0, int n1, int n2,
+                                             const double* __restrict__ tT,
+                                             const double* __restrict__ tV, T* __restrict__ e,
+                                             double* __restrict__ wpart) {
+  __shared__ double red[32 * 7];
+  const long np = (long)n0 * n1 * n2;
+  const long mu = blockIdx.x;
+  const int a = (int)(mu % n0), b = (int)((mu / n0) % n1), c = (int)(mu / ((long)n0 * n1));
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long nu = threadIdx.x; nu < np; nu += blockDim.x) {
+    int a2 = (int)(nu % n0), b2 = (int)((nu / n0) % n1), c2 = (int)(nu / ((long)n0 * n1));
+    int da = a - a2, db = b - b2, dc = c - c2;
+    if (da < 0) da += n0;
+    if (db < 0) db += n1;
+    if (dc < 0) dc += n2;
+    const long m = da + (long)n0 * (db + (long)n1 * dc);
+    const double qv = (double)q[nu];
+    v[0] += tT[m] * qv;
+    if (VIR)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[1 + k] += tV[k * np + m] * qv;
+  }
+  block_sum_n<7>(v, red);
+  if (threadIdx.x == 0) {
+    e[mu] = (T)v[0];
+    if (VIR) {
+      const double hq = 0.5 * (double)q[mu];
+      for (int k = 0; k < 6; ++k) wpart[6 * mu + k] = hq * v[1 + k];
+    }
+  }
+}
+
+template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
+  const int l = p->levels;
+  const Level& Lt = p->lv[l];
+  double* wp = p->d_wpart + 6 * p->wpart_top;
+  if (vir)
+    k_top<T, true><<<Lt.np, 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+                                          p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
+  else
+    k_top<T, false><<<Lt.np, 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+                                           p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
+  return 1;
+}
+
+// -------------------------------------------------------------- prolongation
+
+// e^{k,tot}_mu = e^k_mu + sum_nu prod_d Phi(mu_d/2 - nu_d) e^{k+1,tot}_nu.
+template <typename T>
+__global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
+                          const T* __restrict__ etc_, int c0, int c1, int c2,
+                          T* __restrict__ etf) {
+  long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long np = (long)f0 * f1 * f2;
+  if (mu >= np) return;
+  int m[3] = {(int)(mu % f0), (int)((mu / f0) % f1), (int)(mu / ((long)f0 * f1))};
+  int nc[3] = {c0, c1, c2};
+  int idx[3][4];
+  T wt[3][4];
+  int cnt[3];
+  for (int d = 0; d < 3; ++d) {
+    if ((m[d] & 1) == 0) {
+      cnt[d] = 1;
+      idx[d][0] = wrapi(m[d] >> 1, nc[d]);
+      wt[d][0] = T(1);
+    } else {
+      cnt[d] = 4;
+      int h = (m[d] - 1) >> 1;  // coarse node left of mu
+      idx[d][0] = wrapi(h - 1, nc[d]);
+      idx[d][1] = wrapi(h, nc[d]);
+      idx[d][2] = wrapi(h + 1, nc[d]);
+      idx[d][3] = wrapi(h + 2, nc[d]);
+      wt[d][0] = T(-0.0625);
+      wt[d][1] = T(0.5625);
+      wt[d][2] = T(0.5625);
+      wt[d][3] = T(-0.0625);
+    }
+  }
+  T acc = 0;
+  for (int c = 0; c < cnt[2]; ++c)
+    for (int b = 0; b < cnt[1]; ++b) {
+      long row = (long)c0 * (idx[1][b] + (long)c1 * idx[2][c]);
+      T s = 0;
+      for (int a = 0; a < cnt[0]; ++a) s += wt[0][a] * etc_[row + idx[0][a]];
+      acc += wt[1][b] * wt[2][c] * s;
+    }
+  etf[mu] = ef[mu] + acc;
+}
+
+template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st) {
+  const Level &F = p->lv[k], &C = p->lv[k + 1];
+  k_prolong<T><<<cdiv(F.np, kBlock), kBlock, 0, st>>>((const T*)p->d_e[k], F.n[0], F.n[1],
+                                                     F.n[2], (const T*)p->d_et[k + 1], C.n[0],
+                                                     C.n[1], C.n[2], (T*)p->d_et[k]);
+  return 1;
+}
+
+// ------------------------------------------------------------- interpolation
+
+// Eq. (interpolation) and its gradient: e_i = sum phi e^{1,tot},
+// F_i = F_i^loc + c_i grad e_i; per-atom energy
+// -1/2 c_i (e0_i + e_i) + 1/2 c_self c_i^2; one energy partial per block.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_interp(
+    const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ et,
+    int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
+    const T* __restrict__ floc, double cself, T* __restrict__ forces,
+    double* __restrict__ atom_energy, double* __restrict__ epart) {
+  __shared__ double sh[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double ea = 0.0;
+  if (i < N) {
+    Vec4<T> p = sp[i];
+    T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
+    T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
+    int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
+    T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+    phi4(u0 - f0, wx, dx);
+    phi4(u1 - f1, wy, dy);
+    phi4(u2 - f2, wz, dz);
+    int ix[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ix[k] = wrapi(b0 - 1 + k, n0);
+    T acc = 0, g0 = 0, g1 = 0, g2 = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int z = wrapi(b2 - 1 + c, n2);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int y = wrapi(b1 - 1 + b, n1);
+        const T* row = et + (long)n0 * (y + (long)n1 * z);
+        T sx = 0, sdx = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T v = row[ix[a]];
+          sx += wx[a] * v;
+          sdx += dx[a] * v;
+        }
+        acc += wy[b] * wz[c] * sx;
+        g0 += wy[b] * wz[c] * sdx;
+        g1 += dy[b] * wz[c] * sx;
+        g2 += wy[b] * dz[c] * sx;
+      }
+    }
+    int o = sidx[i];
+    T ci = p.w;
+    forces[3 * (size_t)o + 0] = floc[3 * (size_t)i + 0] + ci * g0 * ih0;
+    forces[3 * (size_t)o + 1] = floc[3 * (size_t)i + 1] + ci * g1 * ih1;
+    forces[3 * (size_t)o + 2] = floc[3 * (size_t)i + 2] + ci * g2 * ih2;
+    double cd = (double)ci;
+    ea = -0.5 * cd * ((double)e0[i] + (double)acc) + 0.5 * cself * cd * cd;
+    if (atom_energy) atom_energy[o] = ea;
+  }
+  double s = block_sum(ea, sh);
+  if (threadIdx.x == 0) epart[blockIdx.x] = s;
+}
+
+template <typename T>
+int launch_interp(Plan* p, T* forces, double* atom_energy, cudaStream_t st) {
+  const Level& L1 = p->lv[1];
+  const int N = (int)p->N;
+  k_interp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+      (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
+      L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,
+      (const T*)p->d_floc, p->c_self, forces, atom_energy, p->d_epart);
+  return 1;
+}
+
+// Stencil launch configuration, decided before the workspace is sized: the
+// tiled kernel (tiles counted in p->stencil_blocks by the caller) when its
+// tile and tap table fit in shared memory (opt in above 48 KB), otherwise
+// the global-memory kernel with one block per 256 nodes.
+template <typename T> int prepare_grid_kernels(Plan* p) {
+  if (p->levels < 2) return MLS6_OK;
+  const int S = kStencilTile + 2 * p->P;
+  p->stencil_smem = align16(sizeof(T) * S * S * S) + sizeof(Vec4<T>) * p->ntaps +
+                    sizeof(int4) * p->nrows;
+  p->stencil_global = p->stencil_smem > 200 * 1024;
+  if (p->stencil_global) {
+    long nodes = 0;
+    for (int k = 1; k < p->levels; ++k) nodes += p->lv[k].np;
+    p->stencil_blocks = cdiv(nodes, kBlock);
+    return MLS6_OK;
+  }
+  if (cudaFuncSetAttribute(k_stencil<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p->stencil_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p->stencil_smem) != cudaSuccess)
+    return MLS6_ERR_CUDA;
+  return MLS6_OK;
+}
+
+#define MLS6_INSTANTIATE(T)                                               \
+  template int launch_anterp<T>(Plan*, cudaStream_t);                     \
+  template int launch_restrict<T>(Plan*, int, cudaStream_t);              \
+  template int launch_stencil<T>(Plan*, bool, cudaStream_t);              \
+  template int launch_top<T>(Plan*, bool, cudaStream_t);                  \
+  template int launch_prolong<T>(Plan*, int, cudaStream_t);               \
+  template int launch_interp<T>(Plan*, T*, double*, cudaStream_t);        \
+  template int prepare_grid_kernels<T>(Plan*);
+MLS6_INSTANTIATE(float)
+MLS6_INSTANTIATE(double)
+#undef MLS6_INSTANTIATE
+
+}  // namespace mls6

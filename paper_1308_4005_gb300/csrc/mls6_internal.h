@@ -1,5 +1,6 @@
-// Internal definitions shared by the host plan (mls6_plan.cpp) and the
-// device code (mls6_eval.cu) of the multilevel summation library.
+// Internal definitions shared by the host plan (mls6_plan.cpp), the launch
+// sequence (mls6_eval.cu) and the kernel translation units of the multilevel
+// summation library.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,16 +14,19 @@ namespace mls6 {
 
 constexpr int kMaxLevels = 12;
 constexpr int kBlock = 256;
+constexpr int kScanTile = 2048;   // cells per block in the cell-count scan
+constexpr int kStencilTile = 8;   // output tile edge of the level-stencil kernel
+constexpr int kStencilThreads = 128;
+constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
 
-// 4-wide position+coefficient records: float4-like for FP32, 32-byte
-// aligned quadruples for FP64.
+// 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
   T x, y, z, w;
 };
 
-// Geometry of the cell list used by the local (g_0) pair sum and by the
-// spatial sort of the atoms.  Cells have width >= a/2 per axis, so
-// neighbours within a lie at most R = ceil(a / w) cells away.
+// Cell list used by the local (g_0) pair sum and for the spatial sort of
+// the atoms.  Cells have width >= a/2 per axis, so neighbours within a lie
+// at most R = ceil(a / w) cells away.
 struct CellGeom {
   int nc[3];        // cells per axis
   int R[3];         // neighbour range per axis
@@ -51,13 +55,20 @@ struct Plan {
   Level lv[kMaxLevels + 1];  // 1-based
   double c_self;             // gamma(0)/a^6
 
-  // level-1 stencil (taps with |m h_1| < 2a), shared by all levels k < l
-  // through the scale 2^(-6(k-1)) (Sec. II.A.4).
-  int ntaps;
-  int pad[3];                // halo width per axis of the padded grid copy
-  std::vector<int> h_tap_m;  // 3 ints per tap
-  std::vector<double> h_tap_g;   // g_1(|m h_1|)
-  std::vector<double> h_tap_v;   // 6 per tap: g_1'(r)/r r_a r_b
+  // Level-1 stencil: taps m with |m h_1| < 2a, shared by all levels k < l
+  // through the scale 2^(-6(k-1)) (Sec. II.A.4).  Taps are grouped in rows
+  // of constant (dy, dz) with dx = -R..R contiguous.
+  int ntaps = 0;
+  int nrows = 0;
+  int P = 0;                      // halo: max |m_d| over all taps and axes
+  std::vector<int> h_rows;        // 4 per row: dy, dz, R, first tap
+  std::vector<double> h_wv;       // 4 per tap: g_1, G = g_1'/r, G dx, G dx^2
+  // stencil launch geometry: one block per 8^3 output tile, all levels k < l
+  int tiles[kMaxLevels + 1][3] = {};
+  long tile_off[kMaxLevels + 1] = {};
+  long stencil_blocks = 0;
+  size_t stencil_smem = 0;
+  bool stencil_global = false;  // tile does not fit in shared memory
   // coarsest level tables
   std::vector<double> h_top_T, h_top_V;
 
@@ -66,6 +77,7 @@ struct Plan {
   int* d_cell_of = nullptr;    // int[N]
   int* d_cell_count = nullptr; // int[ncell]
   int* d_cell_start = nullptr; // int[ncell + 1]
+  int* d_scan = nullptr;       // tile sums of the cell-count scan
   void* d_sorted = nullptr;    // Vec4<T>[N] sorted by cell
   int* d_sorted_idx = nullptr; // int[N] original index of sorted atom
   void* d_e0 = nullptr;        // T[N] local potential (sorted order)
@@ -73,28 +85,39 @@ struct Plan {
   void* d_q[kMaxLevels + 1] = {};
   void* d_e[kMaxLevels + 1] = {};
   void* d_et[kMaxLevels + 1] = {};
-  void* d_qpad = nullptr;      // padded copy of a level grid (largest level < l)
-  int* d_tap_off = nullptr;    // per level: linear offsets in the padded grid
-  void* d_tap_g = nullptr;     // T[ntaps]
-  void* d_tap_v = nullptr;     // T[6 * ntaps]
+  int* d_rows = nullptr;       // int4 per row
+  void* d_wv = nullptr;        // Vec4<T> per tap
   double* d_top_T = nullptr;
   double* d_top_V = nullptr;
   double* d_epart = nullptr;   // energy partials (interpolation blocks)
-  double* d_wpart = nullptr;   // virial partials: pair blocks, stencil blocks, top
+  double* d_wpart = nullptr;   // virial partials: pair blocks | stencil blocks | top nodes
   long n_epart = 0, n_wpart = 0, n_pair_blocks = 0;
-  int* d_scan = nullptr;       // tile sums of the cell-count scan
-  long wpart_pair = 0;         // offsets into d_wpart
-  long wpart_lvl[kMaxLevels + 1] = {};
-  long wpart_top = 0;
+  long wpart_stencil = 0, wpart_top = 0;  // offsets (in 6-double records)
   double* d_out = nullptr;     // [0] energy, [1..6] virial
   int* d_flag = nullptr;       // device error flags
   double* h_out = nullptr;     // pinned host staging of d_out
 
-  // per-stage event timing (mls6_profile)
+  // per-stage event timing (mls6_profile): start/end event per stage
   static constexpr int kStages = 9;
   bool prof = false;
-  cudaEvent_t ev[kStages + 1] = {};
+  cudaEvent_t ev_s[kStages] = {}, ev_e[kStages] = {};
   int launches = 0;            // kernels launched by the last evaluation
+
+  // execution: internal non-blocking streams (main chain, pair branch),
+  // ordered against the caller's stream by events; optional CUDA graph of
+  // the whole evaluation, re-captured when its pointers or options change.
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  bool use_graph = true;
+  cudaGraphExec_t gexec = nullptr;
+  struct GraphKey {
+    const void *pos, *c, *forces, *energy, *virial, *atom_energy;
+    bool vir, prof;
+    bool operator==(const GraphKey& o) const {
+      return pos == o.pos && c == o.c && forces == o.forces && energy == o.energy &&
+             virial == o.virial && atom_energy == o.atom_energy && vir == o.vir && prof == o.prof;
+    }
+  } gkey = {};
 
   size_t elem() const { return prec == MLS6_FP64 ? sizeof(double) : sizeof(float); }
 };
@@ -105,9 +128,22 @@ double dgamma_over_rho(double rho);  // gamma'(rho)/rho
 double g_level(int k, int l, double a, double r);
 double dg_level_over_r(int k, int l, double a, double r);
 
-// device launch sequence (mls6_eval.cu)
+// launch sequence (mls6_eval.cu)
 int eval_launch(Plan* p, const void* pos, const void* c, void* forces, double* energy,
                 double* virial, double* atom_energy);
 int upload_tables(Plan* p);
+
+// kernel launchers; each returns the number of kernels it launched
+template <typename T> int launch_bin(Plan* p, const T* pos, const T* c, cudaStream_t st);
+template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st);
+template <typename T> int launch_anterp(Plan* p, cudaStream_t st);
+template <typename T> int launch_restrict(Plan* p, int k, cudaStream_t st);
+template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st);
+template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st);
+template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st);
+template <typename T>
+int launch_interp(Plan* p, T* forces, double* atom_energy, cudaStream_t st);
+template <typename T> int prepare_grid_kernels(Plan* p);
+int launch_reduce(Plan* p, bool vir, cudaStream_t st);
 
 }  // namespace mls6

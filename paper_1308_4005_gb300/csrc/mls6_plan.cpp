@@ -235,9 +235,8 @@ static int grid_dims_impl(const double box[3], double h, int levels, int n_out[3
 static void free_plan(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_pos_w, p->d_cell_of, p->d_cell_count, p->d_cell_start, p->d_sorted,
-                  p->d_sorted_idx, p->d_e0, p->d_floc, p->d_qpad, p->d_tap_off, p->d_tap_g,
-                  p->d_tap_v, p->d_top_T, p->d_top_V, p->d_epart, p->d_wpart, p->d_out,
-                  p->d_flag, p->d_scan};
+                  p->d_sorted_idx, p->d_e0, p->d_floc, p->d_rows, p->d_wv, p->d_top_T,
+                  p->d_top_V, p->d_epart, p->d_wpart, p->d_out, p->d_flag, p->d_scan};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 1; k <= kMaxLevels; ++k) {
@@ -246,8 +245,16 @@ static void free_plan(Plan* p) {
     if (p->d_et[k] && p->d_et[k] != p->d_e[k]) cudaFree(p->d_et[k]);
   }
   if (p->h_out) cudaFreeHost(p->h_out);
-  for (int i = 0; i <= Plan::kStages; ++i)
-    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  for (int i = 0; i < Plan::kStages; ++i) {
+    if (p->ev_s[i]) cudaEventDestroy(p->ev_s[i]);
+    if (p->ev_e[i]) cudaEventDestroy(p->ev_e[i]);
+  }
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  cudaEvent_t evs[] = {p->ev_in, p->ev_out, p->ev_fork, p->ev_join};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (p->cs) cudaStreamDestroy(p->cs);
+  if (p->cs2) cudaStreamDestroy(p->cs2);
   delete p;
 }
 
@@ -313,31 +320,37 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
     p->cg.R[d] = (int)std::ceil(a / p->cg.w[d] * (1.0 - 1e-12));
     p->cg.ncell *= nc;
   }
-  // level-1 stencil taps |m h_1| < 2a (used on levels 1..l-1)
-  p->ntaps = 0;
-  for (int d = 0; d < 3; ++d) p->pad[d] = 0;
+  // Level-1 stencil taps |m h_1| < 2a (used on levels 1..l-1), in rows of
+  // constant (dy, dz) with contiguous dx = -R..R (the cross-section of the
+  // cutoff sphere).  Per tap: g_1(r), G = g_1'(r)/r, G dx, G dx^2.
+  p->ntaps = p->nrows = p->P = 0;
   if (levels >= 2) {
-    int M[3];
-    for (int d = 0; d < 3; ++d) M[d] = (int)std::ceil(2.0 * a / p->lv[1].h[d]) + 1;
-    for (int m2 = -M[2]; m2 <= M[2]; ++m2)
-      for (int m1 = -M[1]; m1 <= M[1]; ++m1)
-        for (int m0 = -M[0]; m0 <= M[0]; ++m0) {
-          double r3[3] = {m0 * p->lv[1].h[0], m1 * p->lv[1].h[1], m2 * p->lv[1].h[2]};
+    const double* h = p->lv[1].h;
+    const double c2 = 4.0 * a * a;
+    int My = (int)std::ceil(2.0 * a / h[1]) + 1, Mz = (int)std::ceil(2.0 * a / h[2]) + 1;
+    for (int dz = -Mz; dz <= Mz; ++dz)
+      for (int dy = -My; dy <= My; ++dy) {
+        double ryz = (dy * h[1]) * (dy * h[1]) + (dz * h[2]) * (dz * h[2]);
+        if (!(ryz < c2)) continue;
+        int R = 0;
+        while (((R + 1) * h[0]) * ((R + 1) * h[0]) + ryz < c2) ++R;
+        p->h_rows.push_back(dy);
+        p->h_rows.push_back(dz);
+        p->h_rows.push_back(R);
+        p->h_rows.push_back(p->ntaps);
+        for (int dx = -R; dx <= R; ++dx) {
+          double r3[3] = {dx * h[0], dy * h[1], dz * h[2]};
           double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
-          if (!(r < 2.0 * a)) continue;
-          p->h_tap_m.push_back(m0);
-          p->h_tap_m.push_back(m1);
-          p->h_tap_m.push_back(m2);
-          p->h_tap_g.push_back(g_level(1, levels, a, r));
-          double gp = r > 0.0 ? dg_level_over_r(1, levels, a, r) : 0.0;
-          double v6[6] = {gp * r3[0] * r3[0], gp * r3[1] * r3[1], gp * r3[2] * r3[2],
-                          gp * r3[0] * r3[1], gp * r3[0] * r3[2], gp * r3[1] * r3[2]};
-          for (double v : v6) p->h_tap_v.push_back(v);
-          p->pad[0] = std::max(p->pad[0], std::abs(m0));
-          p->pad[1] = std::max(p->pad[1], std::abs(m1));
-          p->pad[2] = std::max(p->pad[2], std::abs(m2));
+          double G = r > 0.0 ? dg_level_over_r(1, levels, a, r) : 0.0;
+          p->h_wv.push_back(g_level(1, levels, a, r));
+          p->h_wv.push_back(G);
+          p->h_wv.push_back(G * dx);
+          p->h_wv.push_back(G * dx * dx);
           p->ntaps++;
         }
+        p->nrows++;
+        p->P = std::max(p->P, std::max(R, std::max(std::abs(dy), std::abs(dz))));
+      }
   }
   // coarsest-level periodic tables
   const Level& top = p->lv[levels];

@@ -29,7 +29,8 @@ MLS6_FP64 = 0
 MLS6_FP32 = 1
 
 # every symbol declared in include/mls6.h
-EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream", "mls6_eval",
+EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream",
+           "mls6_set_graph", "mls6_eval",
            "mls6_eval_atoms", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
            "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_destroy",
            "mls6_status_string")
@@ -64,6 +65,8 @@ def load(path: str = LIB_PATH):
     L.mls6_plan.restype = C.c_int
     L.mls6_set_stream.argtypes = [C.c_void_p, C.c_void_p]
     L.mls6_set_stream.restype = C.c_int
+    L.mls6_set_graph.argtypes = [C.c_void_p, C.c_int]
+    L.mls6_set_graph.restype = C.c_int
     L.mls6_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p]
     L.mls6_eval.restype = C.c_int
@@ -133,6 +136,10 @@ def mls6_plan(box, N, a, h, levels, order=3, precision=MLS6_FP64):
 def mls6_set_stream(plan, stream_handle):
     _check(load().mls6_set_stream(C.c_void_p(plan), C.c_void_p(stream_handle or 0)),
            "mls6_set_stream")
+
+
+def mls6_set_graph(plan, enable=True):
+    _check(load().mls6_set_graph(C.c_void_p(plan), int(bool(enable))), "mls6_set_graph")
 
 
 def mls6_eval(plan, pos_ptr, c_ptr, forces_ptr, energy_ptr, virial_ptr):

@@ -215,3 +215,68 @@ def test_cube1m_fp32_sampled(gpu_lib, orc):
     assert np.abs(g["F"][idx] - o["F"]).max() <= TOL32["F"] * rms
     assert np.abs(g["eatom"][idx] - o["eatom"]).max() <= TOL32["eatom"] * np.abs(o["eatom"]).max()
     assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-12)
+
+
+# ------------------------------------------------------ execution modes
+
+def _fixed_buffers(N, prec):
+    import torch
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return (torch.empty((N, 4), dtype=dt, device="cuda"),
+            torch.empty((N, 3), dtype=dt, device="cuda"),
+            torch.zeros(8, dtype=torch.float64, device="cuda"))
+
+
+def test_graph_replay_matches_eager_and_tracks_inputs(gpu_lib):
+    """The captured graph replays with the same buffers; new positions written
+    into the same input buffer are picked up; eager launches agree."""
+    import torch
+
+    box, a, h, l = (9.0, 9.0, 12.0), 2.2, 0.75, 3
+    x1, c = I.uniform_atoms(41, 500, box)
+    x2, _ = I.uniform_atoms(42, 500, box)
+    plan = gpu_lib.Plan(box, 500, a, h, l, precision="fp64")
+    pos, F, out = _fixed_buffers(500, "fp64")
+    res = {}
+    for mode in ("graph", "eager"):
+        gpu_lib.mls6_set_graph(plan.handle, mode == "graph")
+        for tag, xx in (("x1", x1), ("x2", x2), ("x1b", x1)):
+            pos.copy_(torch.tensor(np.c_[xx, c], dtype=torch.float64))
+            rc = gpu_lib.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), out.data_ptr(),
+                                   out.data_ptr() + 8)
+            assert rc == 0
+            torch.cuda.synchronize()
+            res[(mode, tag)] = (out[:7].cpu().numpy().copy(), F.cpu().numpy().copy())
+    for tag in ("x1", "x2", "x1b"):
+        (og, Fg), (oe, Fe) = res[("graph", tag)], res[("eager", tag)]
+        assert np.allclose(og, oe, rtol=1e-14, atol=0)
+        assert np.abs(Fg - Fe).max() <= 1e-13 * np.abs(Fe).max()
+    assert not np.allclose(res[("graph", "x1")][0], res[("graph", "x2")][0])
+    assert np.allclose(res[("graph", "x1")][0], res[("graph", "x1b")][0], rtol=1e-14, atol=0)
+
+
+def test_caller_stream_ordering(gpu_lib):
+    """Work on the caller's stream before and after mls6_eval is ordered
+    with the library's internal streams."""
+    import torch
+
+    box, a, h, l = (9.0, 9.0, 9.0), 2.2, 0.75, 3
+    x, c = I.uniform_atoms(43, 400, box)
+    ref = gpu_eval(gpu_lib, box, a, h, l, x, c, "fp64", atom_energy=False)
+    s = torch.cuda.Stream()
+    plan = gpu_lib.Plan(box, 400, a, h, l, precision="fp64", stream=s.cuda_stream)
+    pos, F, out = _fixed_buffers(400, "fp64")
+    src = torch.tensor(np.c_[x, c], dtype=torch.float64).pin_memory()
+    Fh = torch.empty((400, 3), dtype=torch.float64).pin_memory()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            pos.zero_()
+            F.fill_(7.0)
+            pos.copy_(src, non_blocking=True)
+            rc = gpu_lib.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), out.data_ptr(),
+                                   out.data_ptr() + 8)
+            assert rc == 0
+            Fh.copy_(F, non_blocking=True)
+            s.synchronize()
+            assert np.abs(Fh.numpy() - ref["F"]).max() <= 1e-13 * np.abs(ref["F"]).max()
