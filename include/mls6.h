@@ -161,6 +161,31 @@ int mls6_stage_times(mls6_plan_t* p, double* ms, int cap, int* launches);
 /* Name of stage i (see mls6_profile), or NULL. */
 const char* mls6_stage_name(int i);
 
+/* Coarsest-level product that allocates no device memory.  The paper has no
+ * counterpart: this is a library convenience for callers that may not
+ * allocate device memory when they call in -- an MD engine that reserves
+ * its whole memory budget up front, code where cudaMalloc/cudaFree would
+ * synchronise the device or is not permitted, or a host framework whose
+ * own allocator must not be bypassed.
+ *   q       device, n[0]*n[1]*n[2] doubles: xi^l on the coarsest grid (x fastest)
+ *   n       host, 3 ints: coarsest grid size; at most 4096 nodes in total,
+ *           larger grids return MLS6_ERR_SIZE
+ *   T, V    device: the tables of mls6_coarse_tables (V may be NULL when
+ *           virial is NULL)
+ *   e       device, n0*n1*n2 doubles, written: e_mu = sum_nu T[(mu-nu) mod n] q_nu
+ *   virial  device, 6 doubles, written (or NULL):
+ *           1/2 sum_mu q_mu sum_nu V_c[(mu-nu) mod n] q_nu
+ *   stream  cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Its scratch (six doubles per node) is one fixed file-scope device array of
+ * 192 KiB that every GPU loading the library holds until the process exits.
+ * The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and every entry a call reads is written by the
+ * same call, so nothing needs clearing, but calls that overlap on the GPU
+ * (different streams, or different host threads) race on it. */
+int mls6_coarse_apply_noalloc(const double* q, const int n[3], const double* T, const double* V,
+                              double* e, double* virial, void* stream);
+
 /* Release the plan and all its device memory.  NULL is ignored. */
 void mls6_destroy(mls6_plan_t* p);
 

@@ -32,8 +32,8 @@ MLS6_FP32 = 1
 EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream",
            "mls6_set_graph", "mls6_eval",
            "mls6_eval_atoms", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
-           "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_destroy",
-           "mls6_status_string")
+           "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_coarse_apply_noalloc",
+           "mls6_destroy", "mls6_status_string")
 
 _lib = None
 _dp = C.POINTER(C.c_double)
@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
     L.mls6_stage_times.restype = C.c_int
     L.mls6_stage_name.argtypes = [C.c_int]
     L.mls6_stage_name.restype = C.c_char_p
+    L.mls6_coarse_apply_noalloc.argtypes = [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]
+    L.mls6_coarse_apply_noalloc.restype = C.c_int
     L.mls6_destroy.argtypes = [C.c_void_p]
     L.mls6_destroy.restype = None
     L.mls6_status_string.argtypes = [C.c_int]
