@@ -44,28 +44,35 @@ __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int s
   atomicAdd(&count[cell], 1);
 }
 
-// Phase 1: per-tile sums of the cell counts.
-__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum) {
+// Phase 1: per-tile sums of the cell counts; the last block to finish
+// (ticket counter, reset by that block) turns the tile sums into exclusive
+// tile offsets in one thread and writes the grand total to start[n].
+__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
+                             int* __restrict__ start, unsigned* __restrict__ ticket) {
   __shared__ double sh[32];
+  __shared__ bool last;
   long base = (long)blockIdx.x * kScanTile;
   int s = 0;
   for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
     if (base + t < n) s += count[base + t];
   double tot = block_sum((double)s, sh);
-  if (threadIdx.x == 0) tsum[blockIdx.x] = (int)tot;
-}
-
-// Phase 2: exclusive scan of the (few hundred) tile sums in one thread;
-// writes the grand total to start[n].
-__global__ void k_scan_top(int* __restrict__ tsum, int ntiles, int* __restrict__ start, long n) {
-  if (threadIdx.x != 0) return;
-  int acc = 0;
-  for (int t = 0; t < ntiles; ++t) {
-    int v = tsum[t];
-    tsum[t] = acc;
-    acc += v;
+  if (threadIdx.x == 0) {
+    tsum[blockIdx.x] = (int)tot;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-  start[n] = acc;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    int acc = 0;
+    for (int t = 0; t < (int)gridDim.x; ++t) {
+      int v = ((volatile int*)tsum)[t];
+      tsum[t] = acc;
+      acc += v;
+    }
+    start[n] = acc;
+    *ticket = 0u;
+  }
 }
 
 // Phase 3: scan inside each tile (256 threads x 8 consecutive cells), write
@@ -123,12 +130,14 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
 
 // Insertion sort of each cell by input index (cells above 256 atoms are
 // left in scatter order: results stay correct, only bitwise
-// reproducibility is lost for them).
+// reproducibility is lost for them).  Also returns the cell's counter to
+// zero for the next binning.
 template <typename T>
 __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
-                           int* __restrict__ sidx) {
+                           int* __restrict__ sidx, int* __restrict__ count) {
   long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncell) return;
+  count[cell] = 0;
   int b = start[cell], e = start[cell + 1];
   if (e - b < 2 || e - b > 256) return;
   for (int i = b + 1; i < e; ++i) {
@@ -156,18 +165,18 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
   }
   const long ncell = p->cg.ncell;
   const long ntiles = cdiv(ncell, kScanTile);
-  cudaMemsetAsync(p->d_cell_count, 0, sizeof(int) * ncell, st);
+  // cell counters start at zero: set at plan creation, reset by k_cellsort
   k_bin<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
                                               p->d_cell_of, p->d_cell_count, p->d_flag);
-  k_scan_tiles<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan);
-  k_scan_top<<<1, 32, 0, st>>>(p->d_scan, (int)ntiles, p->d_cell_start, ncell);
+  k_scan_tiles<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start,
+                                          reinterpret_cast<unsigned*>(p->d_flag + 2));
   k_scan_final<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
   k_scatter<T><<<cdiv(N, kBlock), kBlock, 0, st>>>((const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
                                                   p->d_cell_start, p->d_cell_count,
                                                   (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
-  k_cellsort<T><<<cdiv(ncell, kBlock), kBlock, 0, st>>>(p->d_cell_start, ncell,
-                                                       (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
-  return 6;
+  k_cellsort<T><<<cdiv(ncell, kBlock), kBlock, 0, st>>>(
+      p->d_cell_start, ncell, (Vec4<T>*)p->d_sorted, p->d_sorted_idx, p->d_cell_count);
+  return 5;
 }
 
 template int launch_bin<float>(Plan*, const float*, const float*, cudaStream_t);

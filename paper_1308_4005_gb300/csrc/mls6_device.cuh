@@ -76,4 +76,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return a[0];
 }
 
+// Fixed-order sum, by one block, of the energy partials (ne doubles) and,
+// if vir, of the virial partials (nw records of 6) into out[0..6].
+// sh: >= 32*7 doubles.
+__device__ __forceinline__ void final_reduce(const double* __restrict__ epart, long ne,
+                                             const double* __restrict__ wpart, long nw, int vir,
+                                             double* __restrict__ out, double* sh) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long k = threadIdx.x; k < ne; k += blockDim.x) v[0] += epart[k];
+  if (vir)
+    for (long k = threadIdx.x; k < nw; k += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[1 + c] += wpart[6 * k + c];
+  block_sum_n<7>(v, sh);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 7; ++c) out[c] = v[c];
+}
+
 }  // namespace mls6

@@ -32,15 +32,7 @@ __global__ void k_reduce(const double* __restrict__ epart, long ne,
                          const double* __restrict__ wpart, long nw, int vir,
                          double* __restrict__ out) {
   __shared__ double sh[32 * 7];
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long k = threadIdx.x; k < ne; k += blockDim.x) v[0] += epart[k];
-  if (vir)
-    for (long k = threadIdx.x; k < nw; k += blockDim.x)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) v[1 + c] += wpart[6 * k + c];
-  block_sum_n<7>(v, sh);
-  if (threadIdx.x == 0)
-    for (int c = 0; c < 7; ++c) out[c] = v[c];
+  final_reduce(epart, ne, wpart, nw, vir, out, sh);
 }
 
 int launch_reduce(Plan* p, bool vir, cudaStream_t st) {
@@ -75,6 +67,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_sorted_idx, sizeof(int) * N);
   rc |= A(&p->d_e0, e * N);
   rc |= A(&p->d_floc, 3 * e * N);
+  p->pair_split = pair_split(N);
   const int l = p->levels;
   for (int k = 1; k <= l; ++k) {
     rc |= A(&p->d_q[k], e * p->lv[k].np);
@@ -105,7 +98,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_top_V, 6 * sizeof(double) * np_top);
   // partial sums: pair blocks | stencil blocks | coarsest nodes
   p->n_epart = std::max(1L, cdiv(N, kBlock));
-  p->n_pair_blocks = std::max(1L, cdiv(N, kBlock));
+  p->n_pair_blocks = std::max(1L, cdiv(N * p->pair_split, kBlock));
   p->wpart_stencil = p->n_pair_blocks;
   p->wpart_top = p->wpart_stencil + p->stencil_blocks;
   p->n_wpart = p->wpart_top + np_top;
@@ -132,6 +125,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   CK(cudaMemcpy(p->d_top_V, p->h_top_V.data(), 6 * sizeof(double) * np_top,
                 cudaMemcpyHostToDevice));
   CK(cudaMemset(p->d_flag, 0, sizeof(int) * 4));
+  CK(cudaMemset(p->d_cell_count, 0, sizeof(int) * p->cg.ncell));  // reset by each binning
   return MLS6_OK;
 }
 
@@ -150,7 +144,10 @@ int upload_tables(Plan* p) {
 // a negative status.
 template <typename T>
 static int enqueue(Plan* p, const T* pos, const T* cc, T* forces, double* energy_dev,
-                   double* virial_dev, bool vir, double* atom_energy) {
+                   double* virial_dev, bool vir, double* atom_energy, bool capturing) {
+  // inside a capture, stage events must be external event-record nodes to
+  // be timeable after the graph runs
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   // Profiling serialises the two branches so that each stage's events time
   // that stage alone.
   cudaStream_t st = p->cs, st2 = p->prof ? p->cs : p->cs2;
@@ -158,15 +155,16 @@ static int enqueue(Plan* p, const T* pos, const T* cc, T* forces, double* energy
   const int l = p->levels;
 #define BEGIN(i, s)                                        \
   do {                                                      \
-    if (p->prof) CK(cudaEventRecordWithFlags(p->ev_s[i], s, cudaEventRecordExternal)); \
+    if (p->prof) CK(cudaEventRecordWithFlags(p->ev_s[i], s, evf)); \
   } while (0)
 #define END(i, s)                                           \
   do {                                                      \
-    if (p->prof) CK(cudaEventRecordWithFlags(p->ev_e[i], s, cudaEventRecordExternal)); \
+    if (p->prof) CK(cudaEventRecordWithFlags(p->ev_e[i], s, evf)); \
   } while (0)
   int nl = 0;
   BEGIN(0, st);
-  CK(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
+  // [0] non-finite flag, [1] interpolation ticket, [2] scan ticket
+  CK(cudaMemsetAsync(p->d_flag, 0, sizeof(int) * 4, st));
   CK(cudaMemsetAsync(p->d_q[1], 0, sizeof(T) * p->lv[1].np, st));
   if (N > 0) nl += launch_bin<T>(p, pos, cc, st);
   END(0, st);
@@ -202,11 +200,12 @@ static int enqueue(Plan* p, const T* pos, const T* cc, T* forces, double* energy
   for (int k = l - 1; k >= 1; --k) nl += launch_prolong<T>(p, k, st);
   END(6, st);
   if (N > 0) CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+  // interpolation; its last block also performs the final reduction
   BEGIN(7, st);
-  if (N > 0) nl += launch_interp<T>(p, forces, atom_energy, st);
+  if (N > 0) nl += launch_interp<T>(p, forces, atom_energy, vir, st);
   END(7, st);
   BEGIN(8, st);
-  nl += launch_reduce(p, vir, st);
+  if (N == 0) nl += launch_reduce(p, vir, st);
   END(8, st);
 #undef BEGIN
 #undef END
@@ -254,7 +253,7 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
         p->gexec = nullptr;
       }
       CK(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
-      int nl = enqueue<T>(p, pos, cc, forces, energy_dev, virial_dev, vir, atom_energy);
+      int nl = enqueue<T>(p, pos, cc, forces, energy_dev, virial_dev, vir, atom_energy, true);
       cudaGraph_t graph = nullptr;
       cudaError_t ce = cudaStreamEndCapture(p->cs, &graph);
       if (nl < 0 || ce != cudaSuccess) {
@@ -273,7 +272,7 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
     }
     CK(cudaGraphLaunch(p->gexec, p->cs));
   } else {
-    int nl = enqueue<T>(p, pos, cc, forces, energy_dev, virial_dev, vir, atom_energy);
+    int nl = enqueue<T>(p, pos, cc, forces, energy_dev, virial_dev, vir, atom_energy, false);
     if (nl < 0) return nl;
     p->launches = nl;
   }

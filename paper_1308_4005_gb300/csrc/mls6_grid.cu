@@ -43,159 +43,9 @@ __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, 
     }
 }
 
-// Brick-tiled anterpolation: one block per kAB^3 brick of finest nodes.  The
-// block walks the cells covering the brick's influence region (atoms whose
-// 4-node support meets the brick, with periodic images as shifts of whole
-// boxes), accumulates their weights into the brick in shared memory and
-// stores the brick once: no global atomics.  Node assignment (base node and
-// fractional offset) is computed from the wrapped position exactly as in
-// the interpolation, so both see the same basis functions.
-constexpr int kAB = 8;
-constexpr int kAnterpThreads = 256;
-constexpr int kAnterpMaxCells = 16;  // cells per axis of an influence region
-
-template <typename T> struct AnterpArgs {
-  int n[3];
-  T ih[3];
-  T h[3];
-  int nc[3];
-  T inv_w[3];
-  int bricks[3];
-};
-
-template <typename T>
-__global__ void __launch_bounds__(kAnterpThreads) k_anterp_tiled(
-    const Vec4<T>* __restrict__ sp, const int* __restrict__ start, AnterpArgs<T> A,
-    T* __restrict__ q) {
-  __shared__ int cst[kAnterpMaxCells * kAnterpMaxCells * kAnterpMaxCells + 1];
-  __shared__ int cmeta[3][2];  // per axis: first unwrapped cell, count
-  __shared__ T acc[kAB * kAB * kAB];
-  __shared__ int s_tot;
-  const int b = blockIdx.x;
-  const int bx = b % A.bricks[0], by = (b / A.bricks[0]) % A.bricks[1],
-            bz = b / (A.bricks[0] * A.bricks[1]);
-  const int lo[3] = {bx * kAB, by * kAB, bz * kAB};
-  for (int i = threadIdx.x; i < kAB * kAB * kAB; i += blockDim.x) acc[i] = T(0);
-  if (threadIdx.x < 3) {
-    const int d = threadIdx.x;
-    // influence region in space: u in [lo-2, lo+kAB+1) nodes
-    T x0 = (T)(lo[d] - 2) * A.h[d], x1 = (T)(lo[d] + kAB + 1) * A.h[d];
-    int c0 = (int)floor(x0 * A.inv_w[d]) - 1, c1 = (int)floor(x1 * A.inv_w[d]) + 1;
-    cmeta[d][0] = c0;
-    cmeta[d][1] = c1 - c0 + 1;
-  }
-  __syncthreads();
-  const int m0 = cmeta[0][1], m1 = cmeta[1][1], m2 = cmeta[2][1];
-  const int ncells = m0 * m1 * m2;
-  for (int c = threadIdx.x; c < ncells; c += blockDim.x) {
-    int ux = cmeta[0][0] + c % m0, uy = cmeta[1][0] + (c / m0) % m1,
-        uz = cmeta[2][0] + c / (m0 * m1);
-    int gc = wrapi(ux, A.nc[0]) + A.nc[0] * (wrapi(uy, A.nc[1]) + A.nc[1] * wrapi(uz, A.nc[2]));
-    cst[c + 1] = start[gc + 1] - start[gc];
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int carry = 0;
-    for (int base = 0; base < ncells; base += 32) {
-      int c = base + threadIdx.x;
-      int v = c < ncells ? cst[c + 1] : 0;
-      int incl = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (threadIdx.x >= o) incl += u;
-      }
-      if (c < ncells) cst[c + 1] = carry + incl;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (threadIdx.x == 0) {
-      cst[0] = 0;
-      s_tot = carry;
-    }
-  }
-  __syncthreads();
-  const int tot = s_tot;
-  for (int s = threadIdx.x; s < tot; s += blockDim.x) {
-    int lo_c = 0, hi_c = ncells;  // cst[lo_c] <= s < cst[hi_c]
-    while (hi_c - lo_c > 1) {
-      int mid = (lo_c + hi_c) >> 1;
-      if (cst[mid] <= s) lo_c = mid; else hi_c = mid;
-    }
-    const int c = lo_c;
-    const int u[3] = {cmeta[0][0] + c % m0, cmeta[1][0] + (c / m0) % m1,
-                      cmeta[2][0] + c / (m0 * m1)};
-    int g[3], shift[3];
-    for (int d = 0; d < 3; ++d) {
-      g[d] = wrapi(u[d], A.nc[d]);
-      shift[d] = (u[d] - g[d]) / A.nc[d];  // whole boxes
-    }
-    const int gc = g[0] + A.nc[0] * (g[1] + A.nc[1] * g[2]);
-    const Vec4<T> p = sp[start[gc] + (s - cst[c])];
-    const T pos[3] = {p.x, p.y, p.z};
-    T w[3][4];
-    int first[3];  // brick-relative index of the first support node
-    bool any = true;
-    for (int d = 0; d < 3; ++d) {
-      T ud = pos[d] * A.ih[d];
-      T fd = floor(ud);
-      phi4w(ud - fd, w[d]);
-      first[d] = (int)fd - 1 + shift[d] * A.n[d] - lo[d];
-      any = any && (first[d] < kAB) && (first[d] + 3 >= 0);
-    }
-    if (!any) continue;
-    for (int kz = 0; kz < 4; ++kz) {
-      const int z = first[2] + kz;
-      if (z < 0 || z >= kAB) continue;
-      for (int ky = 0; ky < 4; ++ky) {
-        const int y = first[1] + ky;
-        if (y < 0 || y >= kAB) continue;
-        const T wyz = p.w * w[1][ky] * w[2][kz];
-        for (int kx = 0; kx < 4; ++kx) {
-          const int x = first[0] + kx;
-          if (x < 0 || x >= kAB) continue;
-          atomicAdd(&acc[x + kAB * (y + kAB * z)], wyz * w[0][kx]);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kAB * kAB * kAB; i += blockDim.x) {
-    const int x = lo[0] + i % kAB, y = lo[1] + (i / kAB) % kAB, z = lo[2] + i / (kAB * kAB);
-    if (x < A.n[0] && y < A.n[1] && z < A.n[2])
-      q[x + (long)A.n[0] * (y + (long)A.n[1] * z)] = acc[i];
-  }
-}
-
-// Cells per axis of an influence region; 0 if the tiled kernel cannot be
-// used (then the per-atom atomic kernel runs).
-static int anterp_region_cells(const Plan* p) {
-  int mx = 0;
-  for (int d = 0; d < 3; ++d) {
-    double span = (kAB + 3) * p->lv[1].h[d] * p->cg.inv_w[d];
-    int m = (int)std::ceil(span) + 3;
-    mx = std::max(mx, m);
-  }
-  return mx <= kAnterpMaxCells ? mx : 0;
-}
-
 template <typename T> int launch_anterp(Plan* p, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
-  if (anterp_region_cells(p) > 0) {
-    AnterpArgs<T> A;
-    long nb = 1;
-    for (int d = 0; d < 3; ++d) {
-      A.n[d] = L1.n[d];
-      A.ih[d] = (T)(1.0 / L1.h[d]);
-      A.h[d] = (T)L1.h[d];
-      A.nc[d] = p->cg.nc[d];
-      A.inv_w[d] = (T)p->cg.inv_w[d];
-      A.bricks[d] = (int)cdiv(L1.n[d], kAB);
-      nb *= A.bricks[d];
-    }
-    k_anterp_tiled<T><<<nb, kAnterpThreads, 0, st>>>((const Vec4<T>*)p->d_sorted,
-                                                     p->d_cell_start, A, (T*)p->d_q[1]);
-    return 1;
-  }
   k_anterp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
       (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (T*)p->d_q[1]);
@@ -256,7 +106,49 @@ template <typename T> struct StencilArgs {
   const int4* rows;     // dy, dz, R, first tap
   const Vec4<T>* wv;    // g_1, G, G dx, G dx^2 per tap
   double hc[6];         // h_x^2, h_y^2, h_z^2, h_x h_y, h_x h_z, h_y h_z (level 1)
+  // coarsest level, run by the blocks after the stencil tiles (if any)
+  long sblocks;         // number of stencil-tile blocks
+  const T* qt;
+  T* et;
+  int nt[3];
+  const double* tT;
+  const double* tV;
+  double* wtop;         // virial partials, one record per coarsest node
 };
+
+// Eq. (last-grid-periodic-transformed) for coarsest node mu in FP64: the
+// block's threads stride over nu; e_mu = sum_nu T[(mu - nu) mod n] q_nu and
+// the virial record 1/2 q_mu sum_nu V[(mu - nu) mod n] q_nu.  sh: 32*7.
+template <typename T, bool VIR>
+__device__ __forceinline__ void coarsest_node(const T* __restrict__ q, int n0, int n1, int n2,
+                                              const double* __restrict__ tT,
+                                              const double* __restrict__ tV, T* __restrict__ e,
+                                              double* __restrict__ wpart, long mu, double* sh) {
+  const long np = (long)n0 * n1 * n2;
+  const int a = (int)(mu % n0), b = (int)((mu / n0) % n1), c = (int)(mu / ((long)n0 * n1));
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long nu = threadIdx.x; nu < np; nu += blockDim.x) {
+    int a2 = (int)(nu % n0), b2 = (int)((nu / n0) % n1), c2 = (int)(nu / ((long)n0 * n1));
+    int da = a - a2, db = b - b2, dc = c - c2;
+    if (da < 0) da += n0;
+    if (db < 0) db += n1;
+    if (dc < 0) dc += n2;
+    const long m = da + (long)n0 * (db + (long)n1 * dc);
+    const double qv = (double)q[nu];
+    v[0] += tT[m] * qv;
+    if (VIR)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[1 + k] += tV[k * np + m] * qv;
+  }
+  block_sum_n<7>(v, sh);
+  if (threadIdx.x == 0) {
+    e[mu] = (T)v[0];
+    if (VIR) {
+      const double hq = 0.5 * (double)q[mu];
+      for (int k = 0; k < 6; ++k) wpart[6 * mu + k] = hq * v[1 + k];
+    }
+  }
+}
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -267,11 +159,20 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 // row (constant dy, dz).  The strain derivative is accumulated per row from
 // three row sums of the node/neighbour products (taps G, G dx, G dx^2), so
 // the six virial components cost 7 FMAs per tap and thread instead of 24.
-template <typename T, bool VIR>
-__global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<T> A,
-                                                             double* __restrict__ wpart) {
+// With G > 1, G groups of 128 threads share a tile and each takes every
+// G-th tap row (more resident warps for small grids); the groups' partial
+// outputs are added in shared memory, their virial terms in the block sum.
+template <typename T, bool VIR, int G>
+__global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> A,
+                                                                 double* __restrict__ wpart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32 * 6];
+  __shared__ double red[32 * 7];
+  __shared__ T part[(G > 1 ? G - 1 : 1) * kStencilThreads * kStencilW];
+  if ((long)blockIdx.x >= A.sblocks) {
+    coarsest_node<T, VIR>(A.qt, A.nt[0], A.nt[1], A.nt[2], A.tT, A.tV, A.et, A.wtop,
+                          (long)blockIdx.x - A.sblocks, red);
+    return;
+  }
   const int S = A.S, P = A.P, S2 = S * S, S3 = S2 * S;
   T* tile = reinterpret_cast<T*>(smem_raw);
   Vec4<T>* wv = reinterpret_cast<Vec4<T>*>(smem_raw + align16(sizeof(T) * S3));
@@ -297,8 +198,8 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<T> A,
   }
   __syncthreads();
 
-  const int lx = (threadIdx.x & 1) * kStencilW, ly = (threadIdx.x >> 1) & 7,
-            lz = threadIdx.x >> 4;
+  const int lt = threadIdx.x % kStencilThreads, grp = threadIdx.x / kStencilThreads;
+  const int lx = (lt & 1) * kStencilW, ly = (lt >> 1) & 7, lz = lt >> 4;
   const bool row_in = (oy + ly < n1) && (oz + lz < n2);
   T qv[kStencilW];
 #pragma unroll
@@ -308,7 +209,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<T> A,
 #pragma unroll
   for (int w = 0; w < kStencilW; ++w) acc[w] = T(0);
   T vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0;
-  for (int r = 0; r < A.nrows; ++r) {
+  for (int r = grp; r < A.nrows; r += G) {
     const int4 ri = rows[r];
     const T* in = tile + (lz + P + ri.y) * S2 + (ly + P + ri.x) * S + (lx + P - ri.z);
     const Vec4<T>* ww = wv + ri.w;
@@ -343,7 +244,19 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<T> A,
     }
   }
   const T scale = A.lv[k].scale;
-  if (row_in) {
+  if (G > 1) {
+    if (grp > 0)
+#pragma unroll
+      for (int w = 0; w < kStencilW; ++w)
+        part[((grp - 1) * kStencilThreads + lt) * kStencilW + w] = acc[w];
+    __syncthreads();
+    if (grp == 0)
+      for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+        for (int w = 0; w < kStencilW; ++w)
+          acc[w] += part[((g2 - 1) * kStencilThreads + lt) * kStencilW + w];
+  }
+  if (row_in && grp == 0) {
     T* e = A.lv[k].e + (ox + lx) + (long)n0 * ((oy + ly) + (long)n1 * (oz + lz));
 #pragma unroll
     for (int w = 0; w < kStencilW; ++w)
@@ -450,8 +363,19 @@ template <typename T> static StencilArgs<T> stencil_args(Plan* p) {
     L.tile_off = p->tile_off[k];
     L.scale = (T)std::ldexp(1.0, -6 * (k - 1));
   }
+  const int l = p->levels;
+  A.sblocks = p->stencil_blocks;
+  A.qt = (const T*)p->d_q[l];
+  A.et = (T*)p->d_e[l];
+  for (int d = 0; d < 3; ++d) A.nt[d] = p->lv[l].n[d];
+  A.tT = p->d_top_T;
+  A.tV = p->d_top_V;
+  A.wtop = p->d_wpart + 6 * p->wpart_top;
   return A;
 }
+
+// Whether the coarsest level rides on the stencil launch (extra blocks).
+bool stencil_fuses_top(const Plan* p) { return p->levels >= 2 && !p->stencil_global && !p->prof; }
 
 template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
   if (p->levels < 2) return 0;
@@ -466,52 +390,33 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
       k_stencil_global<T, false><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
     return 1;
   }
-  if (vir)
-    k_stencil<T, true><<<p->stencil_blocks, kStencilThreads, p->stencil_smem, st>>>(A, wp);
-  else
-    k_stencil<T, false><<<p->stencil_blocks, kStencilThreads, p->stencil_smem, st>>>(A, wp);
+  const long nb = p->stencil_blocks + (stencil_fuses_top(p) ? p->lv[p->levels].np : 0);
+  const size_t sm = p->stencil_smem;
+  switch (p->stencil_groups * 2 + (vir ? 1 : 0)) {
+    case 2 * 4 + 1: k_stencil<T, true, 4><<<nb, kStencilThreads * 4, sm, st>>>(A, wp); break;
+    case 2 * 4 + 0: k_stencil<T, false, 4><<<nb, kStencilThreads * 4, sm, st>>>(A, wp); break;
+    case 2 * 2 + 1: k_stencil<T, true, 2><<<nb, kStencilThreads * 2, sm, st>>>(A, wp); break;
+    case 2 * 2 + 0: k_stencil<T, false, 2><<<nb, kStencilThreads * 2, sm, st>>>(A, wp); break;
+    case 2 * 1 + 1: k_stencil<T, true, 1><<<nb, kStencilThreads, sm, st>>>(A, wp); break;
+    default: k_stencil<T, false, 1><<<nb, kStencilThreads, sm, st>>>(A, wp); break;
+  }
   return 1;
 }
 
 // ------------------------------------------------------------ coarsest level
 
-// Eq. (last-grid-periodic-transformed) in FP64: one block per coarsest node
-// mu, threads stride over nu, e_mu = sum_nu T[(mu - nu) mod n] q_nu; the
-// virial adds 1/2 q_mu sum_nu V[(mu - nu) mod n] q_nu.
+// Coarsest level on its own launch: one block per node.
 template <typename T, bool VIR>
 __global__ void __launch_bounds__(128) k_top(const T* __restrict__ q, int n0, int n1, int n2,
                                              const double* __restrict__ tT,
                                              const double* __restrict__ tV, T* __restrict__ e,
                                              double* __restrict__ wpart) {
   __shared__ double red[32 * 7];
-  const long np = (long)n0 * n1 * n2;
-  const long mu = blockIdx.x;
-  const int a = (int)(mu % n0), b = (int)((mu / n0) % n1), c = (int)(mu / ((long)n0 * n1));
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long nu = threadIdx.x; nu < np; nu += blockDim.x) {
-    int a2 = (int)(nu % n0), b2 = (int)((nu / n0) % n1), c2 = (int)(nu / ((long)n0 * n1));
-    int da = a - a2, db = b - b2, dc = c - c2;
-    if (da < 0) da += n0;
-    if (db < 0) db += n1;
-    if (dc < 0) dc += n2;
-    const long m = da + (long)n0 * (db + (long)n1 * dc);
-    const double qv = (double)q[nu];
-    v[0] += tT[m] * qv;
-    if (VIR)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v[1 + k] += tV[k * np + m] * qv;
-  }
-  block_sum_n<7>(v, red);
-  if (threadIdx.x == 0) {
-    e[mu] = (T)v[0];
-    if (VIR) {
-      const double hq = 0.5 * (double)q[mu];
-      for (int k = 0; k < 6; ++k) wpart[6 * mu + k] = hq * v[1 + k];
-    }
-  }
+  coarsest_node<T, VIR>(q, n0, n1, n2, tT, tV, e, wpart, (long)blockIdx.x, red);
 }
 
 template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
+  if (stencil_fuses_top(p)) return 0;  // ran as extra blocks of the stencil launch
   const int l = p->levels;
   const Level& Lt = p->lv[l];
   double* wp = p->d_wpart + 6 * p->wpart_top;
@@ -581,13 +486,24 @@ template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st) {
 // Eq. (interpolation) and its gradient: e_i = sum phi e^{1,tot},
 // F_i = F_i^loc + c_i grad e_i; per-atom energy
 // -1/2 c_i (e0_i + e_i) + 1/2 c_self c_i^2; one energy partial per block.
+// The last block to finish (ticket counter, reset by that block) sums all
+// energy and virial partials in a fixed order into out[0..6].
+struct ReduceArgs {
+  const double* wpart;
+  long nw;
+  int vir;
+  double* out;
+  unsigned* ticket;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_interp(
     const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ et,
     int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, double cself, T* __restrict__ forces,
-    double* __restrict__ atom_energy, double* __restrict__ epart) {
-  __shared__ double sh[32];
+    double* __restrict__ atom_energy, double* __restrict__ epart, ReduceArgs R) {
+  __shared__ double sh[32 * 7];
+  __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double ea = 0.0;
   if (i < N) {
@@ -633,17 +549,29 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     if (atom_energy) atom_energy[o] = ea;
   }
   double s = block_sum(ea, sh);
-  if (threadIdx.x == 0) epart[blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    epart[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(R.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
+    if (threadIdx.x == 0) *R.ticket = 0u;
+  }
 }
 
 template <typename T>
-int launch_interp(Plan* p, T* forces, double* atom_energy, cudaStream_t st) {
+int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
+  ReduceArgs R = {p->d_wpart, p->n_wpart, vir ? 1 : 0, p->d_out,
+                  reinterpret_cast<unsigned*>(p->d_flag + 1)};
   k_interp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
       L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,
-      (const T*)p->d_floc, p->c_self, forces, atom_energy, p->d_epart);
+      (const T*)p->d_floc, p->c_self, forces, atom_energy, p->d_epart, R);
   return 1;
 }
 
@@ -663,10 +591,19 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
     p->stencil_blocks = cdiv(nodes, kBlock);
     return MLS6_OK;
   }
-  if (cudaFuncSetAttribute(k_stencil<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)p->stencil_smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_stencil<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)p->stencil_smem) != cudaSuccess)
+  // tap-row groups per tile: the smallest of 1, 2, 4 giving about 24
+  // resident warps per SM on a 152-SM GPU
+  p->stencil_groups = 1;
+  while (p->stencil_groups < 4 && p->stencil_blocks * 4 * p->stencil_groups < 152L * 24)
+    p->stencil_groups *= 2;
+  const int sm = (int)p->stencil_smem;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (cudaFuncSetAttribute(k_stencil<T, true, 1>, attr, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, false, 1>, attr, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, true, 2>, attr, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, false, 2>, attr, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, true, 4>, attr, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_stencil<T, false, 4>, attr, sm) != cudaSuccess)
     return MLS6_ERR_CUDA;
   return MLS6_OK;
 }
@@ -677,7 +614,7 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
   template int launch_stencil<T>(Plan*, bool, cudaStream_t);              \
   template int launch_top<T>(Plan*, bool, cudaStream_t);                  \
   template int launch_prolong<T>(Plan*, int, cudaStream_t);               \
-  template int launch_interp<T>(Plan*, T*, double*, cudaStream_t);        \
+  template int launch_interp<T>(Plan*, T*, double*, bool, cudaStream_t);  \
   template int prepare_grid_kernels<T>(Plan*);
 MLS6_INSTANTIATE(float)
 MLS6_INSTANTIATE(double)

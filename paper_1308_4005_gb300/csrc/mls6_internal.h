@@ -69,6 +69,7 @@ struct Plan {
   long stencil_blocks = 0;
   size_t stencil_smem = 0;
   bool stencil_global = false;  // tile does not fit in shared memory
+  int stencil_groups = 1;       // thread groups (of 128) sharing one tile
   // coarsest level tables
   std::vector<double> h_top_T, h_top_V;
 
@@ -80,6 +81,7 @@ struct Plan {
   int* d_scan = nullptr;       // tile sums of the cell-count scan
   void* d_sorted = nullptr;    // Vec4<T>[N] sorted by cell
   int* d_sorted_idx = nullptr; // int[N] original index of sorted atom
+  int pair_split = 1;          // lanes per atom in the pair kernel
   void* d_e0 = nullptr;        // T[N] local potential (sorted order)
   void* d_floc = nullptr;      // T[3N] local forces (sorted order)
   void* d_q[kMaxLevels + 1] = {};
@@ -142,8 +144,9 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st);
 template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st);
 template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st);
 template <typename T>
-int launch_interp(Plan* p, T* forces, double* atom_energy, cudaStream_t st);
+int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st);
 template <typename T> int prepare_grid_kernels(Plan* p);
 int launch_reduce(Plan* p, bool vir, cudaStream_t st);
+int pair_split(long N);  // lanes per atom of the pair kernel (mls6_pair.cu)
 
 }  // namespace mls6

@@ -21,52 +21,67 @@ template <typename T> struct PairArgs {
 template <typename T> __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
 
-template <typename T, bool VIR>
+// S consecutive lanes share one atom: the (2R+1)^2 rows of neighbour cells
+// (constant dy, dz; the dx cells of a row are contiguous in the sorted
+// array, split only where the row wraps periodically) are dealt round-robin
+// to the S lanes, and the lanes' partial sums are combined by shuffles.
+// S > 1 raises the number of resident warps for small systems, where one
+// lane per atom leaves the SMs waiting on memory latency.
+template <typename T, bool VIR, int S>
 __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
                                                   PairArgs<T> g, T* __restrict__ e0,
                                                   T* __restrict__ floc,
                                                   double* __restrict__ wpart) {
   __shared__ double sh[32 * 6];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gid / S, sub = gid % S;
   T e = 0, fx = 0, fy = 0, fz = 0;
   T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
   T ci = 0;
   if (i < N) {
-    Vec4<T> pi = sp[i];
+    const Vec4<T> pi = sp[i];
     ci = pi.w;
-    int cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
-    int cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
-    int cz = min(max((int)(pi.z * g.inv_w[2]), 0), g.nc[2] - 1);
-    for (int dz = -g.R[2]; dz <= g.R[2]; ++dz) {
-      int z = cz + dz, iz = wrapi(z, g.nc[2]);
-      T sz = (T)((z - iz) / g.nc[2]) * g.box.L[2];
-      for (int dy = -g.R[1]; dy <= g.R[1]; ++dy) {
-        int y = cy + dy, iy = wrapi(y, g.nc[1]);
-        T sy = (T)((y - iy) / g.nc[1]) * g.box.L[1];
-        int row = g.nc[0] * (iy + g.nc[1] * iz);
-        int dx = -g.R[0];
-        while (dx <= g.R[0]) {
-          int x = cx + dx, ix = wrapi(x, g.nc[0]);
-          int wx = (x - ix) / g.nc[0];
-          int last = min(g.R[0], dx + (g.nc[0] - 1 - ix));  // same image run
-          T sx = (T)wx * g.box.L[0];
-          bool same = (wx == 0) && (y == iy) && (z == iz);
-          int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
-          for (int j = j0; j < j1; ++j) {
-            if (same && j == i) continue;
-            Vec4<T> pj = sp[j];
-            T ddx = (pj.x - pi.x) + sx, ddy = (pj.y - pi.y) + sy, ddz = (pj.z - pi.z) + sz;
-            T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < g.a2) {
-              T inv = rcp(r2);
-              T inv3 = inv * inv * inv;
-              T s = r2 * g.ia2, s2 = s * s, s3 = s2 * s, s6 = s3 * s3;
-              T s5 = s3 * s2;
-              T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
-              T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
-              e += pj.w * g0;
-              T cg = pj.w * gp;
+    const int cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
+    const int cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
+    const int cz = min(max((int)(pi.z * g.inv_w[2]), 0), g.nc[2] - 1);
+    const int ny = 2 * g.R[1] + 1, nrows = (2 * g.R[2] + 1) * ny;
+    for (int r = sub; r < nrows; r += S) {
+      const int dz = r / ny - g.R[2], dy = r % ny - g.R[1];
+      const int z = cz + dz, iz = wrapi(z, g.nc[2]);
+      const T sz = (T)((z - iz) / g.nc[2]) * g.box.L[2];
+      const int y = cy + dy, iy = wrapi(y, g.nc[1]);
+      const T sy = (T)((y - iy) / g.nc[1]) * g.box.L[1];
+      const int row = g.nc[0] * (iy + g.nc[1] * iz);
+      int dx = -g.R[0];
+      while (dx <= g.R[0]) {
+        const int x = cx + dx, ix = wrapi(x, g.nc[0]);
+        const int wx = (x - ix) / g.nc[0];
+        const int last = min(g.R[0], dx + (g.nc[0] - 1 - ix));  // same image run
+        const T sx = (T)wx * g.box.L[0];
+        const bool same = (wx == 0) && (y == iy) && (z == iz);
+        const int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
+        // candidates four at a time: the four loads are issued together;
+        // slots past the run (or the atom itself) are never inside a
+        for (int j = j0; j < j1; j += 4) {
+          Vec4<T> pj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pj[u] = sp[min(j + u, j1 - 1)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const T ddx = (pj[u].x - pi.x) + sx, ddy = (pj[u].y - pi.y) + sy,
+                    ddz = (pj[u].z - pi.z) + sz;
+            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            const bool valid = (j + u < j1) && !(same && j + u == i);
+            if (valid && r2 < g.a2) {
+              const T inv = rcp(r2);
+              const T inv3 = inv * inv * inv;
+              const T s = r2 * g.ia2, s2 = s * s, s3 = s2 * s, s6 = s3 * s3;
+              const T s5 = s3 * s2;
+              const T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
+              const T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
+              e += pj[u].w * g0;
+              const T cg = pj[u].w * gp;
               fx += cg * ddx;
               fy += cg * ddy;
               fz += cg * ddz;
@@ -80,17 +95,26 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
               }
             }
           }
-          dx = last + 1;
         }
+        dx = last + 1;
       }
     }
+  }
+#pragma unroll
+  for (int o = S / 2; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+  }
+  if (i < N && sub == 0) {
     e0[i] = e;
     floc[3 * (size_t)i + 0] = -ci * fx;
     floc[3 * (size_t)i + 1] = -ci * fy;
     floc[3 * (size_t)i + 2] = -ci * fz;
   }
   if (VIR) {
-    double hc = 0.5 * (double)ci;
+    const double hc = 0.5 * (double)ci;
     double wv[6] = {hc * w0, hc * w1, hc * w2, hc * w3, hc * w4, hc * w5};
     block_sum_n<6>(wv, sh);
     if (threadIdx.x == 0)
@@ -98,8 +122,28 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
   }
 }
 
-template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
+// Lanes per atom: the smallest of 1, 2, 4, 8 that gives about 48 resident
+// warps per SM on a 152-SM GPU.
+int pair_split(long N) {
+  const long want = 152L * 48 * 32;
+  int s = 1;
+  while (s < 8 && N * s < want) s *= 2;
+  return s;
+}
+
+template <typename T, int S>
+static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, cudaStream_t st) {
   const int N = (int)p->N;
+  const long nb = cdiv((long)N * S, kBlock);
+  if (vir)
+    k_pair<T, true, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+                                              pg, (T*)p->d_e0, (T*)p->d_floc, p->d_wpart);
+  else
+    k_pair<T, false, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+                                               pg, (T*)p->d_e0, (T*)p->d_floc, p->d_wpart);
+}
+
+template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
   PairArgs<T> pg;
   for (int d = 0; d < 3; ++d) {
     pg.box.L[d] = (T)p->L[d];
@@ -112,14 +156,12 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
   pg.ia2 = (T)(1.0 / (p->a * p->a));
   pg.ia6 = (T)std::pow(p->a, -6.0);
   pg.ia8 = (T)std::pow(p->a, -8.0);
-  if (vir)
-    k_pair<T, true><<<cdiv(N, kBlock), kBlock, 0, st>>>(
-        (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
-        p->d_wpart);
-  else
-    k_pair<T, false><<<cdiv(N, kBlock), kBlock, 0, st>>>(
-        (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
-        p->d_wpart);
+  switch (p->pair_split) {
+    case 8: launch_s<T, 8>(p, pg, vir, st); break;
+    case 4: launch_s<T, 4>(p, pg, vir, st); break;
+    case 2: launch_s<T, 2>(p, pg, vir, st); break;
+    default: launch_s<T, 1>(p, pg, vir, st); break;
+  }
   return 1;
 }
 
