@@ -41,6 +41,10 @@ FLOP_TAP = 2            # one stencil tap (multiply-add) per node
 FLOP_TAP_VIR = 12       # ... plus six virial multiply-adds
 
 
+# arithmetic of each precision mode (pair/grid transfers; level stencils)
+DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -48,8 +52,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="slab65536")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched workloads: keep the seeded configuration")
     ap.add_argument("--dwell", type=float, default=1.5,
                     help="seconds of untimed back-to-back evaluations before timing")
     return ap.parse_args()
@@ -180,7 +186,7 @@ def workload_arrays(name, rank, precision):
 
         w = dataclasses.replace(w, seed=w.seed + 1000 * rank)
     x, c = I.generate(w)
-    dt = np.float32 if precision == "fp32" else np.float64
+    dt = np.float64 if precision == "fp64" else np.float32
     return w, x.astype(dt), c.astype(dt)
 
 
@@ -278,6 +284,63 @@ def run_reference(args):
     return 0
 
 
+def run_reference_batch(args):
+    """Oracle arm of the batched workload: each step times the FP64 oracle on
+    one replica (cycling through the replicas by size rank), grid part in full
+    and local part on a 1/32 sample, and reports atoms per second."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import dataclasses
+
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1308_4005_gb300 import inputs as I
+
+    nrep = 256 if args.workload == "batch256" else 16
+    ws = I.batch_workloads(B=nrep)
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    rng = np.random.default_rng(11)
+    order = sorted(range(nrep), key=lambda r: ws[r].N)
+    picks = [order[(k * nrep) // max(1, args.steps + args.warmup)]
+             for k in range(args.steps + args.warmup)]
+    atoms = secs = 0.0
+    for k, r in enumerate(picks):
+        w = ws[r]
+        w = dataclasses.replace(w, levels=I_auto_levels(w))
+        x, c = I.generate(w)
+        S = min(w.N, max(1, w.N // 32))
+        t_grid, t_loc = _oracle_parts(O, w, x, c, S, rng)
+        if k >= args.warmup:
+            atoms += w.N
+            secs += t_grid + t_loc * w.N / S
+    value = atoms / secs
+    line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "replicas": nrep, "a": ws[0].a,
+                       "h": ws[0].h, "levels": "auto per replica"},
+            "cpu_baseline": {"value": value, "unit": "atom-evals/s", "cores": O.threads(),
+                             "kind": "oracle",
+                             "sample": (f"each step: one replica (spread over the size range), "
+                                        "FP64 oracle grid part in full + local part for 1/32 "
+                                        "of its atoms, extrapolated")},
+            "e2e": {"value": value, "unit": "atom-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def I_auto_levels(w):
+    from paper_1308_4005_gb300 import mls6
+
+    return mls6.mls6_auto_levels(w.box, w.h)
+
+
 def config_of(w, args, world):
     return {"workload": w.name, "N_per_gpu": w.N, "box": list(w.box), "a": w.a, "h": w.h,
             "levels": w.levels, "order": 3, "precision": args.precision,
@@ -301,8 +364,8 @@ def run_ours(args):
     B.build()
     mls6.load()
     w, x, c = workload_arrays(args.workload, rank, args.precision)
-    dt = torch.float32 if args.precision == "fp32" else torch.float64
-    esz = 4 if args.precision == "fp32" else 8
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    esz = 8 if args.precision == "fp64" else 4
     N = w.N
     stream = torch.cuda.Stream(device=dev)
     plan = mls6.Plan(w.box, N, w.a, w.h, w.levels, precision=args.precision,
@@ -426,7 +489,13 @@ def run_ours(args):
     if dom in work:
         bound, amount, unit, note = work[dom]
         ach = amount / (stage_ms[dom] / 1e3)
-        if bound == "alu":
+        if dom == "stencil" and info.get("stencil_kind") == 2:
+            bound, peak = "tensor", tensor_peak()
+            peak_note = ("MEASURED_PEAKS.json bf16_tflops (of measured; cuBLAS bf16 burst): the "
+                         "stencil runs as BF16 mma with split operands")
+        if bound == "tensor":
+            pass
+        elif bound == "alu":
             peak, peak_note = fp32_peak, (f"FP32 FMA peak derived: {SMS} SMs x "
                                           f"{FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz "
                                           "(median sampled SM clock)")
@@ -440,7 +509,7 @@ def run_ours(args):
     line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": config_of(w, args, world),
             "e2e": {"value": e2e_value, "unit": "atom-evals/s",
                     "h2d_bytes_per_step": int(pos_h.numel() * pos_h.element_size()),
@@ -460,6 +529,194 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- batched replicas
+
+def run_batch(args):
+    """Batched replicas (256 uneven systems, about 5.0M atoms): one graph
+    launch per step over all replicas; value = atoms of all replicas per
+    second.  Autotuned (branch count, kernel shapes) before the timed
+    region unless --no-tune."""
+    import numpy as np
+    import torch
+
+    from paper_1308_4005_gb300 import build as B
+    from paper_1308_4005_gb300 import inputs as I
+    from paper_1308_4005_gb300 import mls6
+
+    world, rank, local = dist_setup(torch)
+    assert torch.cuda.is_available(), "bench.py --impl ours needs a GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    mls6.load()
+    nrep = 256 if args.workload == "batch256" else 16
+    ws = I.batch_workloads(B=nrep, seed=I.SEED_BASE + 3 + 1000 * rank)
+    t0 = time.time()
+    x, c, off = I.generate_batch(ws, processes=min(16, os.cpu_count() or 1))
+    t_gen = time.time() - t0
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    Ntot = int(off[-1])
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.time()
+    bt = mls6.Batch([w.box for w in ws], [w.N for w in ws], ws[0].a, ws[0].h, 0,
+                    precision=args.precision)
+    t_plan = time.time() - t0
+    mls6.mls6_batch_set_stream(bt.handle, stream.cuda_stream)
+    pos_h = torch.tensor(np.c_[x, c], dtype=dt).pin_memory()
+    pos = torch.empty((Ntot, 4), dtype=dt, device=dev)
+    F = torch.empty((Ntot, 3), dtype=dt, device=dev)
+    F_h = torch.empty((Ntot, 3), dtype=dt).pin_memory()
+    E = torch.zeros(nrep, dtype=torch.float64, device=dev)
+    W = torch.zeros((nrep, 6), dtype=torch.float64, device=dev)
+    E_h = torch.zeros(nrep, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        pos.copy_(pos_h, non_blocking=True)
+    stream.synchronize()
+    seed_info = bt.info()
+    t_tune = None
+    if not args.no_tune:
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            bt.tune(pos, reps=3)
+        t_tune = time.time() - t0
+    info = bt.info()
+
+    def step():
+        rc = mls6.mls6_batch_eval(bt.handle, pos.data_ptr(), 0, F.data_ptr(), E.data_ptr(),
+                                  W.data_ptr())
+        if rc:
+            raise mls6.MLS6Error(rc, "mls6_batch_eval")
+
+    sampler = ClockSampler(gpu_smi_id(torch, local))
+    t_dwell0 = time.time()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        stream.synchronize()
+    info = bt.info()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    value, total_ms = job_throughput(torch, sum(a.elapsed_time(b) for a, b in ev), Ntot,
+                                     args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+    # end to end: positions in from pinned host memory, forces and energies out
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev2[k][0].record(stream)
+            pos.copy_(pos_h, non_blocking=True)
+            step()
+            F_h.copy_(F, non_blocking=True)
+            E_h.copy_(E, non_blocking=True)
+            ev2[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e2e_value, _ = job_throughput(torch, sum(a.elapsed_time(b) for a, b in ev2), Ntot,
+                                  args.steps, world, dev)
+    sampler.stop()
+    clocks = sampler.summary(t_dwell0, time.time())
+
+    # per-replica stage times: each replica's plan alone, stages serialised
+    stage_acc = {}
+    work_pair = work_sten = 0.0
+    esz = 8 if args.precision == "fp64" else 4
+    for r, w in enumerate(ws):
+        ph = mls6.mls6_batch_replica(bt.handle, r)
+        pinfo = mls6.mls6_plan_info(ph)
+        mls6.mls6_profile(ph, True)
+        sl = slice(int(off[r]), int(off[r + 1]))
+        with torch.cuda.stream(stream):
+            mls6.mls6_set_stream(ph, stream.cuda_stream)
+            for _ in range(2):
+                rc = mls6.mls6_eval(ph, pos[sl].data_ptr(), 0, F[sl].data_ptr(), 0,
+                                    W[r].data_ptr())
+                if rc:
+                    raise mls6.MLS6Error(rc, "replica eval")
+            st, _ = mls6.mls6_stage_times(ph)
+        mls6.mls6_profile(ph, False)
+        for name, ms in st.items():
+            stage_acc[name] = stage_acc.get(name, 0.0) + ms
+        lv = pinfo["n_grid"]
+        work_pair += count_pairs(x[sl], np.array(w.box), w.a) * (FLOP_PAIR + FLOP_PAIR_VIR)
+        work_sten += sum(n[0] * n[1] * n[2] for n in lv[:-1]) * pinfo["ntaps"] * \
+            (FLOP_TAP + FLOP_TAP_VIR)
+    dom = max(stage_acc, key=lambda k: stage_acc[k])
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roof = None
+    if dom in ("pair", "stencil"):
+        amount = (work_pair if dom == "pair" else work_sten) / 1e12
+        ach = amount / (stage_acc[dom] / 1e3)
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "work": f"sum over the {nrep} replicas of the {dom} kernel's algorithmic flops",
+                "peak_source": (f"FP32 FMA peak derived: {SMS} SMs x {FP32_LANES_PER_SM} lanes "
+                                f"x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)"),
+                "avg_launch_ms": stage_acc[dom] / nrep,
+                "timing": ("CUDA events around the stage, each replica's plan evaluated alone "
+                           "with serialised stages after the timed region")}
+    line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": args.workload, "replicas": nrep, "atoms_per_gpu": Ntot,
+                       "N_min": int(min(w.N for w in ws)), "N_max": int(max(w.N for w in ws)),
+                       "a": ws[0].a, "h": ws[0].h, "levels": "auto per replica",
+                       "precision": args.precision,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "branches": info["branches"], "seed_branches": seed_info["branches"],
+                       "autotune_s": t_tune, "plan_s": t_plan, "generate_s": t_gen,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "e2e": {"value": e2e_value, "unit": "atom-evals/s",
+                    "h2d_bytes_per_step": int(pos_h.numel() * pos_h.element_size()),
+                    "d2h_bytes_per_step": int(F_h.numel() * F_h.element_size() + 8 * nrep)},
+            "gpu_launches": int(info["launches"]) * args.steps,
+            "roofline": roof,
+            "stages_ms_sum_over_replicas": stage_acc, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mid = sorted(range(nrep), key=lambda r: ws[r].N)[nrep // 2]
+        sl = slice(int(off[mid]), int(off[mid + 1]))
+        wm = ws[mid]
+        import dataclasses
+
+        wm = dataclasses.replace(wm, levels=info["levels"][mid])
+        cb = oracle_baseline(wm, x[sl], c[sl])
+        cb["sample"] = f"median-size replica {mid} (N={wm.N}): " + cb["sample"]
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bt.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -470,6 +727,10 @@ def hbm_peak():
 
 def main():
     args = parse()
+    if args.workload.startswith("batch"):
+        if args.impl == "reference":
+            return run_reference_batch(args)
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -63,8 +63,13 @@ typedef enum {
 
 typedef enum {
   MLS6_FP64 = 0,  /* every step in double precision */
-  MLS6_FP32 = 1   /* pair kernel and grids in float; coarsest level, energy
+  MLS6_FP32 = 1,  /* pair kernel and grids in float; coarsest level, energy
                      and virial accumulation in double */
+  MLS6_MIXED = 2  /* as MLS6_FP32, but the level stencils run on the tensor
+                     cores with BF16 hi+lo split operands and FP32
+                     accumulation (relative error of a stencil product
+                     <= 3 * 2^-18); used when every tap row spans at most 8
+                     nodes either side (2a/h_1 < 9), else the FP32 stencil */
 } mls6_precision;
 
 /* Finest-grid size for a box (per axis the multiple of 2^(levels-1) nearest
@@ -160,6 +165,113 @@ int mls6_stage_times(mls6_plan_t* p, double* ms, int cap, int* launches);
 
 /* Name of stage i (see mls6_profile), or NULL. */
 const char* mls6_stage_name(int i);
+
+/* Level count used when mls6_plan is given levels = 0: the largest l (1..12)
+ * for which every axis of the coarsest grid of the hierarchy that
+ * mls6_grid_dims(box, h, l) gives has at least 4 points (1 if already l = 2
+ * fails).  The paper leaves l to the user (Sec. II.A.4: any number of
+ * nested grids; Sec. IV: the coarsest product costs N_l^2 and must stay
+ * small); this rule keeps N_l at 64..~500 nodes.  Host only; returns l >= 1
+ * or a negative status. */
+int mls6_auto_levels(const double box[3], double h);
+
+/* Kernel shapes of a plan.  pair_split: lanes per atom of the local pair
+ * kernel (1, 2, 4 or 8); stencil_groups: thread groups of 128 sharing one
+ * 8^3 stencil tile (1, 2 or 4; ignored when the stencil tile does not fit in
+ * shared memory); 0 keeps the current value.  The defaults come from the
+ * plan's size (about 48 resident warps per SM for the pair kernel, 24 for
+ * the stencil).  A shape changes the order of floating-point sums (results
+ * move at rounding level), never what is summed.  Waits for the plan's
+ * streams; the next evaluation re-captures its graph. */
+int mls6_set_tuning(mls6_plan_t* p, int pair_split, int stencil_groups);
+
+/* Which level-stencil kernel the plan runs: 0 shared-memory tiles on the
+ * CUDA cores (FP64 / FP32), 1 global-memory fallback (tile and taps beyond
+ * the shared-memory budget), 2 tensor cores (MLS6_MIXED), -1 none (l = 1). */
+int mls6_stencil_kind(const mls6_plan_t* p);
+int mls6_get_tuning(const mls6_plan_t* p, int* pair_split, int* stencil_groups);
+
+/* ---------------------------------------------------------------------
+ * Batches: B independent replicas (each its own box, atom count and grid
+ * hierarchy, same a, h, levels rule, order and precision) evaluated by a
+ * single CUDA graph launch.  The replicas' kernel sequences are captured
+ * into K independent chains of the graph (branches), replicas assigned to
+ * chains by longest-processing-time-first on the cost model below.  Each
+ * replica runs the kernels of a single plan with the same shapes, so its
+ * results equal mls6_eval's on such a plan bit for bit.
+ * --------------------------------------------------------------------- */
+typedef struct mls6_batch_t mls6_batch_t;
+
+/* Model run time (seconds) of one evaluation, after the paper's cost
+ * model (Sec. IV, Eq. cost: C_local (a/d)^3 N + C_grids (a/h)^3 V/h^3 with
+ * d^3 = V/N) extended by a per-atom term (binning, anterpolation,
+ * interpolation), the coarsest product N_l^2 and a per-launch latency:
+ *   coef[0] (a^3 N/V) N + coef[1] (a/h)^3 (V/h^3) 8/7 + coef[2] N
+ *   + coef[3] N_l^2 + coef[4] (8 + 2(l-1)).
+ * coef: 5 doubles or NULL for the built-in values (from GB300 stage
+ * timings).  Host only. */
+int mls6_cost_model(const double box[3], int64_t N, double a, double h, int levels,
+                    const double* coef, double* cost);
+
+/* Longest-processing-time-first assignment of B jobs of the given costs to
+ * K chains: jobs in decreasing cost (stable), each to the chain with the
+ * least load so far (lowest index on ties).  branch_of: B ints, written;
+ * load: K doubles (may be NULL), written.  Host only. */
+int mls6_lpt_assign(int B, const double* cost, int K, int* branch_of, double* load);
+
+/* Create a batch.  boxes: B x 3 doubles; N: B atom counts; a, h, levels
+ * (0 = mls6_auto_levels per replica), order, precision as for mls6_plan.
+ * The batch owns the B plans and a few per-replica words.  On error no
+ * batch is returned and everything allocated is released. */
+int mls6_batch_plan(mls6_batch_t** out, int B, const double* boxes, const int64_t* N, double a,
+                    double h, int levels, int order, int precision);
+
+/* Stream ordering as for mls6_set_stream. */
+int mls6_batch_set_stream(mls6_batch_t* b, void* stream);
+
+/* Evaluate all replicas.  pos, c, forces: device arrays concatenating the
+ * replicas in order (replica r starts at atom offsets[r] of
+ * mls6_batch_size), laid out as for mls6_eval.  energy: B doubles, virial:
+ * 6B doubles (NULL skips the virial), host or device; host pointers make the
+ * call wait and report MLS6_ERR_NONFINITE if any replica saw a non-finite
+ * input.  The first call with a set of pointers captures the graph. */
+int mls6_batch_eval(mls6_batch_t* b, const void* pos, const void* c, void* forces,
+                    double* energy, double* virial);
+
+/* Autotune on the given inputs: times whole-batch launches (median of reps,
+ * with the virial) while it varies the branch count over 1..64, then the
+ * lanes per atom and the stencil groups of every replica one power of two
+ * below and above their defaults, keeping each change that lowers the time.
+ * Leaves the best configuration applied; best_sec (may be NULL) receives
+ * its time.  forces is overwritten. */
+int mls6_batch_tune(mls6_batch_t* b, const void* pos, const void* c, void* forces, int reps,
+                    double* best_sec);
+
+/* Set the configuration directly: branches (0 keeps it; chains are
+ * re-assigned by LPT), per-replica pair_split / stencil_groups arrays of B
+ * ints (NULL keeps them; 0 entries keep that replica's value). */
+int mls6_batch_set_config(mls6_batch_t* b, int branches, const int* pair_split,
+                          const int* stencil_groups);
+
+/* Current configuration; each array of B ints/doubles may be NULL:
+ * branch count, per replica lanes per atom, stencil groups, chain index,
+ * model cost (seconds) and level count; launches: kernels in the graph
+ * captured last (0 before the first evaluation). */
+int mls6_batch_info(const mls6_batch_t* b, int* branches, int* pair_split, int* stencil_groups,
+                    int* branch_of, double* cost, int* levels, int* launches);
+
+/* The plan of replica r, owned by the batch (valid until the batch is
+ * destroyed): for mls6_plan_info, mls6_profile / mls6_stage_times on a
+ * single evaluation of that replica, or mls6_debug_grid.  Changing its
+ * shapes with mls6_set_tuning directly bypasses the batch's graph: use
+ * mls6_batch_set_config instead. */
+int mls6_batch_replica(mls6_batch_t* b, int r, mls6_plan_t** plan);
+
+/* Number of replicas and the B+1 atom offsets (may be NULL). */
+int mls6_batch_size(const mls6_batch_t* b, int* B, int64_t* offsets);
+
+/* Release the batch, its plans and all their device memory.  NULL is ignored. */
+void mls6_batch_destroy(mls6_batch_t* b);
 
 /* Coarsest-level product that allocates no device memory.  The paper has no
  * counterpart: this is a library convenience for callers that may not

@@ -14,56 +14,89 @@ template <typename T> struct BinArgs {
   int nc[3];
 };
 
+// Also writes, for the fixed-point anterpolation, the block's largest |c|
+// (bmax[block]; reduced by the scan's last block).
 template <typename T>
 __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
                       BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
-                      int* __restrict__ count, int* __restrict__ flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const T* p = pos + (size_t)i * stride;
-  T x = p[0], y = p[1], z = p[2];
-  T c = cc ? cc[i] : p[3];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(c))) {
-    atomicOr(flag, 1);
-    x = y = z = c = T(0);
+                      int* __restrict__ count, int* __restrict__ flag, T* __restrict__ bmax) {
+  __shared__ T wmax[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  T cabs = T(0);
+  if (i < N) {
+    const T* p = pos + (size_t)i * stride;
+    T x = p[0], y = p[1], z = p[2];
+    T c = cc ? cc[i] : p[3];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(c))) {
+      atomicOr(flag, 1);
+      x = y = z = c = T(0);
+    }
+    x = wrapx(x, g.box.L[0], g.box.invL[0]);
+    y = wrapx(y, g.box.L[1], g.box.invL[1]);
+    z = wrapx(z, g.box.L[2], g.box.invL[2]);
+    int cx = min(max((int)(x * g.inv_w[0]), 0), g.nc[0] - 1);
+    int cy = min(max((int)(y * g.inv_w[1]), 0), g.nc[1] - 1);
+    int cz = min(max((int)(z * g.inv_w[2]), 0), g.nc[2] - 1);
+    int cell = cx + g.nc[0] * (cy + g.nc[1] * cz);
+    cell_of[i] = cell;
+    Vec4<T> v;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    v.w = c;
+    posw[i] = v;
+    atomicAdd(&count[cell], 1);
+    cabs = fabs(c);
   }
-  x = wrapx(x, g.box.L[0], g.box.invL[0]);
-  y = wrapx(y, g.box.L[1], g.box.invL[1]);
-  z = wrapx(z, g.box.L[2], g.box.invL[2]);
-  int cx = min(max((int)(x * g.inv_w[0]), 0), g.nc[0] - 1);
-  int cy = min(max((int)(y * g.inv_w[1]), 0), g.nc[1] - 1);
-  int cz = min(max((int)(z * g.inv_w[2]), 0), g.nc[2] - 1);
-  int cell = cx + g.nc[0] * (cy + g.nc[1] * cz);
-  cell_of[i] = cell;
-  Vec4<T> v;
-  v.x = x;
-  v.y = y;
-  v.z = z;
-  v.w = c;
-  posw[i] = v;
-  atomicAdd(&count[cell], 1);
+  for (int o = 16; o > 0; o >>= 1) cabs = fmax(cabs, __shfl_xor_sync(0xffffffffu, cabs, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = cabs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m = T(0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+    bmax[blockIdx.x] = m;
+  }
 }
 
-// Phase 1: per-tile sums of the cell counts; the last block to finish
-// (ticket counter, reset by that block) turns the tile sums into exclusive
-// tile offsets in one thread and writes the grand total to start[n].
+// Phase 1: per-tile sums and maxima of the cell counts; the last block to
+// finish (ticket counter, reset by that block) turns the tile sums into
+// exclusive tile offsets in one thread, writes the grand total to start[n],
+// and reduces the maxima for the anterpolation's fixed-point scale: the
+// largest cell population to flag[3], the largest |c| (from the binning
+// blocks' bmax) to flag[4..5] as a double.
+template <typename T>
 __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
-                             int* __restrict__ start, unsigned* __restrict__ ticket) {
+                             int* __restrict__ tmax, const T* __restrict__ bmax, int nbin,
+                             int* __restrict__ start, int* __restrict__ flag) {
   __shared__ double sh[32];
+  __shared__ int shm[32];
+  __shared__ double shc[32];
   __shared__ bool last;
+  unsigned* ticket = reinterpret_cast<unsigned*>(flag + 2);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   long base = (long)blockIdx.x * kScanTile;
-  int s = 0;
+  int s = 0, m = 0;
   for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
-    if (base + t < n) s += count[base + t];
-  double tot = block_sum((double)s, sh);
+    if (base + t < n) {
+      const int v = count[base + t];
+      s += v;
+      m = max(m, v);
+    }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) shm[wid] = m;
+  double tot = block_sum((double)s, sh);  // synchronises: shm complete
   if (threadIdx.x == 0) {
+    int mm = 0;
+    for (int w = 0; w < nw; ++w) mm = max(mm, shm[w]);
     tsum[blockIdx.x] = (int)tot;
+    tmax[blockIdx.x] = mm;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
     int acc = 0;
     for (int t = 0; t < (int)gridDim.x; ++t) {
       int v = ((volatile int*)tsum)[t];
@@ -72,6 +105,29 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
     }
     start[n] = acc;
     *ticket = 0u;
+  }
+  int mp = 0;
+  double mc = 0.0;
+  for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x)
+    mp = max(mp, ((volatile int*)tmax)[t]);
+  for (int t = threadIdx.x; t < nbin; t += blockDim.x) mc = fmax(mc, (double)bmax[t]);
+  for (int o = 16; o > 0; o >>= 1) {
+    mp = max(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+    mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    shm[wid] = mp;
+    shc[wid] = mc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < nw; ++w) {
+      mp = max(mp, shm[w]);
+      mc = fmax(mc, shc[w]);
+    }
+    flag[3] = mp;
+    *reinterpret_cast<double*>(flag + 4) = mc;
   }
 }
 
@@ -166,10 +222,12 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
   const long ncell = p->cg.ncell;
   const long ntiles = cdiv(ncell, kScanTile);
   // cell counters start at zero: set at plan creation, reset by k_cellsort
-  k_bin<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
-                                              p->d_cell_of, p->d_cell_count, p->d_flag);
-  k_scan_tiles<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start,
-                                          reinterpret_cast<unsigned*>(p->d_flag + 2));
+  const int nbin = (int)cdiv(N, kBlock);
+  k_bin<T><<<nbin, kBlock, 0, st>>>(pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
+                                    p->d_cell_of, p->d_cell_count, p->d_flag, (T*)p->d_bmax);
+  k_scan_tiles<T><<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_scan + ntiles,
+                                             (const T*)p->d_bmax, nbin, p->d_cell_start,
+                                             p->d_flag);
   k_scan_final<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
   k_scatter<T><<<cdiv(N, kBlock), kBlock, 0, st>>>((const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
                                                   p->d_cell_start, p->d_cell_count,

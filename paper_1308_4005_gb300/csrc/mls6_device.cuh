@@ -70,6 +70,31 @@ template <int NV> __device__ __forceinline__ void block_sum_n(double (&v)[NV], d
     }
 }
 
+// Block-wide sums of NV values accumulated in the kernel's precision T:
+// each warp sums in T, warp leaders promote to double and thread 0 adds the
+// warp totals in double (fixed order).  Keeps FP64 work, which runs at a
+// small fraction of the FP32 rate, to NV values per warp.  Results valid in
+// thread 0 (out); sh: >= 32*NV doubles.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_lo(T (&v)[NV], double (&out)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sh[c * 32 + wid] = (double)v[c];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[c * 32 + w];
+      out[c] = s;
+    }
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   double a[1] = {v};
   block_sum_n<1>(a, sh);
@@ -91,6 +116,44 @@ __device__ __forceinline__ void final_reduce(const double* __restrict__ epart, l
   block_sum_n<7>(v, sh);
   if (threadIdx.x == 0)
     for (int c = 0; c < 7; ++c) out[c] = v[c];
+}
+
+// Eq. (last-grid-periodic-transformed) for coarsest node mu in FP64, by
+// one warp: the lanes stride over nu; e_mu = sum_nu T[(mu - nu) mod n] q_nu
+// and the virial record 1/2 q_mu sum_nu V[(mu - nu) mod n] q_nu.  Partial
+// sums are combined by shuffles in a fixed order.
+template <typename T, bool VIR>
+__device__ __forceinline__ void coarsest_node(const T* __restrict__ q, int n0, int n1, int n2,
+                                              const double* __restrict__ tT,
+                                              const double* __restrict__ tV, T* __restrict__ e,
+                                              double* __restrict__ wpart, int mu) {
+  const int lane = threadIdx.x & 31;
+  const int np = n0 * n1 * n2;
+  const int a = mu % n0, b = (mu / n0) % n1, c = mu / (n0 * n1);
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int nu = lane; nu < np; nu += 32) {
+    const int a2 = nu % n0, b2 = (nu / n0) % n1, c2 = nu / (n0 * n1);
+    int da = a - a2, db = b - b2, dc = c - c2;
+    if (da < 0) da += n0;
+    if (db < 0) db += n1;
+    if (dc < 0) dc += n2;
+    const int m = da + n0 * (db + n1 * dc);
+    const double qv = (double)q[nu];
+    v[0] += tT[m] * qv;
+    if (VIR)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[1 + k] += tV[(size_t)k * np + m] * qv;
+  }
+#pragma unroll
+  for (int k = 0; k < (VIR ? 7 : 1); ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0) {
+    e[mu] = (T)v[0];
+    if (VIR) {
+      const double hq = 0.5 * (double)q[mu];
+      for (int k = 0; k < 6; ++k) wpart[6 * (size_t)mu + k] = hq * v[1 + k];
+    }
+  }
 }
 
 }  // namespace mls6

@@ -36,7 +36,7 @@ __global__ void k_reduce(const double* __restrict__ epart, long ne,
 }
 
 int launch_reduce(Plan* p, bool vir, cudaStream_t st) {
-  k_reduce<<<1, kBlock, 0, st>>>(p->d_epart, p->n_epart, p->d_wpart, p->n_wpart, vir ? 1 : 0,
+  k_reduce<<<1, kBlock, 0, st>>>(p->d_epart, p->n_epart, p->d_wpart, wpart_used(p), vir ? 1 : 0,
                                  p->d_out);
   return 1;
 }
@@ -62,7 +62,8 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_cell_of, sizeof(int) * N);
   rc |= A((void**)&p->d_cell_count, sizeof(int) * p->cg.ncell);
   rc |= A((void**)&p->d_cell_start, sizeof(int) * (p->cg.ncell + 1));
-  rc |= A((void**)&p->d_scan, sizeof(int) * std::max(1L, cdiv(p->cg.ncell, kScanTile)));
+  rc |= A((void**)&p->d_scan, 2 * sizeof(int) * std::max(1L, cdiv(p->cg.ncell, kScanTile)));
+  rc |= A(&p->d_bmax, sizeof(T) * std::max(1L, cdiv(N, kBlock)));
   rc |= A(&p->d_sorted, sizeof(Vec4<T>) * N);
   rc |= A((void**)&p->d_sorted_idx, sizeof(int) * N);
   rc |= A(&p->d_e0, e * N);
@@ -89,6 +90,13 @@ template <typename T> static int upload_tables_t(Plan* p) {
   }
   rc = prepare_grid_kernels<T>(p);  // may switch to the global-memory stencil
   if (rc) return rc;
+  if (stencil_tc_eligible(p)) {  // mixed precision: tensor-core stencil tiles
+    tc_geometry(p);
+    p->stencil_tc = true;
+    p->stencil_global = false;
+    rc = prepare_stencil_tc(p);
+    if (rc) return rc;
+  }
   if (l >= 2) {
     rc |= A((void**)&p->d_rows, sizeof(int) * 4 * p->nrows);
     rc |= A(&p->d_wv, sizeof(Vec4<T>) * p->ntaps);
@@ -98,14 +106,18 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_top_V, 6 * sizeof(double) * np_top);
   // partial sums: pair blocks | stencil blocks | coarsest nodes
   p->n_epart = std::max(1L, cdiv(N, kBlock));
-  p->n_pair_blocks = std::max(1L, cdiv(N * p->pair_split, kBlock));
-  p->wpart_stencil = p->n_pair_blocks;
-  p->wpart_top = p->wpart_stencil + p->stencil_blocks;
-  p->n_wpart = p->wpart_top + np_top;
+  // room for the largest lane split, so that the split can be retuned
+  // without reallocation; records a smaller split does not write stay zero
+  p->n_pair_blocks = std::max(1L, cdiv(N * kPairSplitMax, kBlock));
+  p->wpart_stencil = 0;
+  p->wpart_top = p->stencil_blocks;
+  p->wpart_pair = p->wpart_top + np_top;
+  p->n_wpart = p->wpart_pair + p->n_pair_blocks;
   rc |= A((void**)&p->d_epart, sizeof(double) * p->n_epart);
   rc |= A((void**)&p->d_wpart, 6 * sizeof(double) * p->n_wpart);
   rc |= A((void**)&p->d_out, 8 * sizeof(double));
-  rc |= A((void**)&p->d_flag, sizeof(int) * 4);
+  rc |= A((void**)&p->d_flag, sizeof(int) * 8);
+  rc |= A(&p->d_q1fx, sizeof(unsigned long long) * p->lv[1].np);
   if (rc) return MLS6_ERR_NOMEM;
   if (cudaMallocHost((void**)&p->h_out, 8 * sizeof(double)) != cudaSuccess) return MLS6_ERR_NOMEM;
 
@@ -121,11 +133,18 @@ template <typename T> static int upload_tables_t(Plan* p) {
                   cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_wv, wv.data(), sizeof(Vec4<T>) * wv.size(), cudaMemcpyHostToDevice));
   }
+  if (p->stencil_tc) {
+    std::vector<uint32_t> tw = tc_weight_table(p);
+    if (cudaMalloc((void**)&p->d_tcw, sizeof(uint32_t) * tw.size()) != cudaSuccess)
+      return MLS6_ERR_NOMEM;
+    CK(cudaMemcpy(p->d_tcw, tw.data(), sizeof(uint32_t) * tw.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(p->d_top_T, p->h_top_T.data(), sizeof(double) * np_top, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(p->d_top_V, p->h_top_V.data(), 6 * sizeof(double) * np_top,
                 cudaMemcpyHostToDevice));
-  CK(cudaMemset(p->d_flag, 0, sizeof(int) * 4));
+  CK(cudaMemset(p->d_flag, 0, sizeof(int) * 8));
   CK(cudaMemset(p->d_cell_count, 0, sizeof(int) * p->cg.ncell));  // reset by each binning
+  CK(cudaMemset(p->d_wpart, 0, 6 * sizeof(double) * p->n_wpart));
   return MLS6_OK;
 }
 
@@ -163,9 +182,12 @@ static int enqueue(Plan* p, const T* pos, const T* cc, T* forces, double* energy
   } while (0)
   int nl = 0;
   BEGIN(0, st);
-  // [0] non-finite flag, [1] interpolation ticket, [2] scan ticket
-  CK(cudaMemsetAsync(p->d_flag, 0, sizeof(int) * 4, st));
-  CK(cudaMemsetAsync(p->d_q[1], 0, sizeof(T) * p->lv[1].np, st));
+  // flags, tickets, maxima (see Plan::d_flag); anterpolation sums
+  CK(cudaMemsetAsync(p->d_flag, 0, sizeof(int) * 8, st));
+  if (N > 0)
+    CK(cudaMemsetAsync(p->d_q1fx, 0, sizeof(T) * p->lv[1].np, st));  // int32 or int64 sums
+  else
+    CK(cudaMemsetAsync(p->d_q[1], 0, sizeof(T) * p->lv[1].np, st));
   if (N > 0) nl += launch_bin<T>(p, pos, cc, st);
   END(0, st);
   if (N > 0) {
@@ -181,7 +203,6 @@ static int enqueue(Plan* p, const T* pos, const T* cc, T* forces, double* energy
   } else {
     // no atoms: grids stay zero; zero the atom-side partial sums
     CK(cudaMemsetAsync(p->d_epart, 0, sizeof(double) * p->n_epart, st));
-    if (vir) CK(cudaMemsetAsync(p->d_wpart, 0, 6 * sizeof(double) * p->n_pair_blocks, st));
     BEGIN(1, st);
     END(1, st);
     BEGIN(2, st);
@@ -292,6 +313,18 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
     if (*reinterpret_cast<int*>(p->h_out + 7)) return MLS6_ERR_NONFINITE;
   }
   return MLS6_OK;
+}
+
+int plan_streams(Plan* p) { return ensure_streams(p); }
+
+int enqueue_eval(Plan* p, const void* pos, const void* c, void* forces, double* energy_dev,
+                 double* virial_dev, bool vir, bool capturing) {
+  if (p->N > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+  if (p->prec == MLS6_FP64)
+    return enqueue<double>(p, (const double*)pos, (const double*)c, (double*)forces, energy_dev,
+                           virial_dev, vir, nullptr, capturing);
+  return enqueue<float>(p, (const float*)pos, (const float*)c, (float*)forces, energy_dev,
+                        virial_dev, vir, nullptr, capturing);
 }
 
 int eval_launch(Plan* p, const void* pos, const void* c, void* forces, double* energy,

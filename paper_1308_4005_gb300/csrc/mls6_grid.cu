@@ -10,13 +10,57 @@ static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------------ anterpolation
 
+// Fixed-point accumulation of the anterpolation: 32-bit integers for the
+// FP32 modes (sums kept below 2^30; resolution ~1e-6 of the largest possible
+// node sum, below FP32 rounding of the grid part), 64-bit for FP64 (below
+// 2^61; resolution ~1e-18 of it).  The conversions stay in the kernel's own
+// precision: FP64 arithmetic is slow on this GPU.
+template <typename T> struct Fixed;
+template <> struct Fixed<float> {
+  using I = int;
+  using U = unsigned int;
+  static constexpr int kBits = 30;
+  __device__ static float pow2(int s) { return __int_as_float((127 + s) << 23); }
+  __device__ static I to_fixed(float v, float scale) { return __float2int_rn(v * scale); }
+  __device__ static float from_fixed(I v, float iscale) { return (float)v * iscale; }
+};
+template <> struct Fixed<double> {
+  using I = long long;
+  using U = unsigned long long;
+  static constexpr int kBits = 61;
+  __device__ static double pow2(int s) { return __longlong_as_double((long long)(1023 + s) << 52); }
+  __device__ static I to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
+  __device__ static double from_fixed(I v, double iscale) { return (double)v * iscale; }
+};
+
+// Scale 2^s with s chosen so that no node sum can exceed 2^kBits in
+// magnitude.  |Phi| <= 1, so a node receives at most |c| per atom within 2h
+// of it (per axis; with periodic images), and those atoms lie in at most
+// `span` cells (cells meeting a box of width 4h), each holding at most
+// flag[3] atoms: bound = flag[3] * span * max|c|.
+template <typename T>
+__device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, double span) {
+  const double cmax = *reinterpret_cast<const double*>(flag + 4);
+  const float bound = (float)((double)flag[3] * span * cmax * (1.0 + 1e-6));
+  if (!(bound > 0.f)) return 0;
+  int e;
+  frexpf(bound, &e);  // bound < 2^e
+  return min(max(Fixed<T>::kBits - e, -120), 120);
+}
+
 // Eq. (anterpolation): q^1_mu += c_j phi_mu(x_j) over the 4x4x4 nodes of
-// every atom (sorted order keeps the atomics of a warp in few cache lines).
+// every atom.  The contributions are rounded to the fixed-point grid 2^-s
+// and added as 64-bit integers: integer addition is associative, so the sums
+// (and everything downstream) do not depend on the order in which the
+// atomics land -- results are reproducible bit for bit.  The rounding
+// (relative 2^-s, s >= ~45 in practice) is far below FP64 parity needs.
 template <typename T>
 __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0,
-                         T ih1, T ih2, T* __restrict__ q) {
+                         T ih1, T ih2, const int* __restrict__ flag, double span,
+                         typename Fixed<T>::U* __restrict__ qfx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span));
   Vec4<T> p = sp[i];
   T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
   T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
@@ -39,17 +83,42 @@ __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, 
       T wyz = p.w * wy[b] * wz[c];
       long rowi = (long)n0 * (iy[b] + (long)n1 * iz[c]);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) atomicAdd(&q[rowi + ix[a]], wyz * wx[a]);
+      for (int a = 0; a < 4; ++a) {
+        const typename Fixed<T>::I v = Fixed<T>::to_fixed(wyz * wx[a], scale);
+        atomicAdd(&qfx[rowi + ix[a]], (typename Fixed<T>::U)v);
+      }
     }
+}
+
+// q^1 = fixed-point sums * 2^-s in the plan's precision.
+template <typename T>
+__global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
+                             const int* __restrict__ flag, double span, T* __restrict__ q) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span));
+  q[i] = Fixed<T>::from_fixed((typename Fixed<T>::I)qfx[i], iscale);
+}
+
+// Cells (with periodic images) that a box of width 4h can meet, product
+// over the axes.
+static double support_span(const Plan* p) {
+  double s = 1.0;
+  for (int d = 0; d < 3; ++d) s *= std::ceil(4.0 * p->lv[1].h[d] / p->cg.w[d]) + 1.0;
+  return s;
 }
 
 template <typename T> int launch_anterp(Plan* p, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
+  const double span = support_span(p);
   k_anterp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
-      (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (T*)p->d_q[1]);
-  return 1;
+      (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), p->d_flag, span,
+      (typename Fixed<T>::U*)p->d_q1fx);
+  k_from_fixed<T><<<cdiv(L1.np, kBlock), kBlock, 0, st>>>(
+      (const typename Fixed<T>::U*)p->d_q1fx, L1.np, p->d_flag, span, (T*)p->d_q[1]);
+  return 2;
 }
 
 // -------------------------------------------------------------- restriction
@@ -116,40 +185,6 @@ template <typename T> struct StencilArgs {
   double* wtop;         // virial partials, one record per coarsest node
 };
 
-// Eq. (last-grid-periodic-transformed) for coarsest node mu in FP64: the
-// block's threads stride over nu; e_mu = sum_nu T[(mu - nu) mod n] q_nu and
-// the virial record 1/2 q_mu sum_nu V[(mu - nu) mod n] q_nu.  sh: 32*7.
-template <typename T, bool VIR>
-__device__ __forceinline__ void coarsest_node(const T* __restrict__ q, int n0, int n1, int n2,
-                                              const double* __restrict__ tT,
-                                              const double* __restrict__ tV, T* __restrict__ e,
-                                              double* __restrict__ wpart, long mu, double* sh) {
-  const long np = (long)n0 * n1 * n2;
-  const int a = (int)(mu % n0), b = (int)((mu / n0) % n1), c = (int)(mu / ((long)n0 * n1));
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long nu = threadIdx.x; nu < np; nu += blockDim.x) {
-    int a2 = (int)(nu % n0), b2 = (int)((nu / n0) % n1), c2 = (int)(nu / ((long)n0 * n1));
-    int da = a - a2, db = b - b2, dc = c - c2;
-    if (da < 0) da += n0;
-    if (db < 0) db += n1;
-    if (dc < 0) dc += n2;
-    const long m = da + (long)n0 * (db + (long)n1 * dc);
-    const double qv = (double)q[nu];
-    v[0] += tT[m] * qv;
-    if (VIR)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v[1 + k] += tV[k * np + m] * qv;
-  }
-  block_sum_n<7>(v, sh);
-  if (threadIdx.x == 0) {
-    e[mu] = (T)v[0];
-    if (VIR) {
-      const double hq = 0.5 * (double)q[mu];
-      for (int k = 0; k < 6; ++k) wpart[6 * mu + k] = hq * v[1 + k];
-    }
-  }
-}
-
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // Eq. (evaluation) on all levels k < l in one launch.  Block = one 8x8x8
@@ -168,9 +203,11 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 7];
   __shared__ T part[(G > 1 ? G - 1 : 1) * kStencilThreads * kStencilW];
-  if ((long)blockIdx.x >= A.sblocks) {
-    coarsest_node<T, VIR>(A.qt, A.nt[0], A.nt[1], A.nt[2], A.tT, A.tV, A.et, A.wtop,
-                          (long)blockIdx.x - A.sblocks, red);
+  if ((long)blockIdx.x >= A.sblocks) {  // coarsest level: one warp per node
+    const int mu = (int)((long)blockIdx.x - A.sblocks) * (int)(blockDim.x >> 5) +
+                   (int)(threadIdx.x >> 5);
+    if (mu < A.nt[0] * A.nt[1] * A.nt[2])
+      coarsest_node<T, VIR>(A.qt, A.nt[0], A.nt[1], A.nt[2], A.tT, A.tV, A.et, A.wtop, mu);
     return;
   }
   const int S = A.S, P = A.P, S2 = S * S, S3 = S2 * S;
@@ -263,13 +300,13 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
       if (ox + lx + w < n0) e[w] = scale * acc[w];
   }
   if (VIR) {
-    const double hs = 0.5 * (double)scale;
-    double v6[6] = {hs * A.hc[0] * (double)vxx, hs * A.hc[1] * (double)vyy,
-                    hs * A.hc[2] * (double)vzz, hs * A.hc[3] * (double)vxy,
-                    hs * A.hc[4] * (double)vxz, hs * A.hc[5] * (double)vyz};
-    block_sum_n<6>(v6, red);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) wpart[6 * b + c] = v6[c];
+    T v6[6] = {vxx, vyy, vzz, vxy, vxz, vyz};
+    double w6[6];
+    block_sum_lo<T, 6>(v6, w6, red);
+    if (threadIdx.x == 0) {
+      const double hs = 0.5 * (double)scale;
+      for (int c = 0; c < 6; ++c) wpart[6 * b + c] = hs * A.hc[c] * w6[c];
+    }
   }
 }
 
@@ -326,13 +363,13 @@ __global__ void __launch_bounds__(kBlock) k_stencil_global(StencilArgs<T> A,
     A.lv[k].e[mu] = scale * acc;
   }
   if (VIR) {
-    const double hs = 0.5 * (double)scale;
-    double v6[6] = {hs * A.hc[0] * (double)vxx, hs * A.hc[1] * (double)vyy,
-                    hs * A.hc[2] * (double)vzz, hs * A.hc[3] * (double)vxy,
-                    hs * A.hc[4] * (double)vxz, hs * A.hc[5] * (double)vyz};
-    block_sum_n<6>(v6, red);
+    // all nodes of a block are on one level unless the block straddles two;
+    // fold the level scale per thread (exact power of two) before summing
+    T v6[6] = {scale * vxx, scale * vyy, scale * vzz, scale * vxy, scale * vxz, scale * vyz};
+    double w6[6];
+    block_sum_lo<T, 6>(v6, w6, red);
     if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = v6[c];
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * A.hc[c] * w6[c];
   }
 }
 
@@ -379,6 +416,7 @@ bool stencil_fuses_top(const Plan* p) { return p->levels >= 2 && !p->stencil_glo
 
 template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
   if (p->levels < 2) return 0;
+  if (p->stencil_tc) return launch_stencil_tc(p, vir, stencil_fuses_top(p), st);
   StencilArgs<T> A = stencil_args<T>(p);
   double* wp = p->d_wpart + 6 * p->wpart_stencil;
   if (p->stencil_global) {
@@ -390,7 +428,9 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
       k_stencil_global<T, false><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
     return 1;
   }
-  const long nb = p->stencil_blocks + (stencil_fuses_top(p) ? p->lv[p->levels].np : 0);
+  const int warps = kStencilThreads * p->stencil_groups / 32;
+  const long nb = p->stencil_blocks +
+                  (stencil_fuses_top(p) ? cdiv(p->lv[p->levels].np, warps) : 0);
   const size_t sm = p->stencil_smem;
   switch (p->stencil_groups * 2 + (vir ? 1 : 0)) {
     case 2 * 4 + 1: k_stencil<T, true, 4><<<nb, kStencilThreads * 4, sm, st>>>(A, wp); break;
@@ -405,14 +445,14 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
 
 // ------------------------------------------------------------ coarsest level
 
-// Coarsest level on its own launch: one block per node.
+// Coarsest level on its own launch: one warp per node, 4 warps per block.
 template <typename T, bool VIR>
 __global__ void __launch_bounds__(128) k_top(const T* __restrict__ q, int n0, int n1, int n2,
                                              const double* __restrict__ tT,
                                              const double* __restrict__ tV, T* __restrict__ e,
                                              double* __restrict__ wpart) {
-  __shared__ double red[32 * 7];
-  coarsest_node<T, VIR>(q, n0, n1, n2, tT, tV, e, wpart, (long)blockIdx.x, red);
+  const int mu = (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5);
+  if (mu < n0 * n1 * n2) coarsest_node<T, VIR>(q, n0, n1, n2, tT, tV, e, wpart, mu);
 }
 
 template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
@@ -421,10 +461,10 @@ template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
   const Level& Lt = p->lv[l];
   double* wp = p->d_wpart + 6 * p->wpart_top;
   if (vir)
-    k_top<T, true><<<Lt.np, 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+    k_top<T, true><<<cdiv(Lt.np, 4), 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
                                           p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
   else
-    k_top<T, false><<<Lt.np, 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+    k_top<T, false><<<cdiv(Lt.np, 4), 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
                                            p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
   return 1;
 }
@@ -566,7 +606,7 @@ template <typename T>
 int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
-  ReduceArgs R = {p->d_wpart, p->n_wpart, vir ? 1 : 0, p->d_out,
+  ReduceArgs R = {p->d_wpart, wpart_used(p), vir ? 1 : 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1)};
   k_interp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
@@ -584,7 +624,7 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
   const int S = kStencilTile + 2 * p->P;
   p->stencil_smem = align16(sizeof(T) * S * S * S) + sizeof(Vec4<T>) * p->ntaps +
                     sizeof(int4) * p->nrows;
-  p->stencil_global = p->stencil_smem > 200 * 1024;
+  p->stencil_global = p->stencil_smem > kStencilSmemMax;
   if (p->stencil_global) {
     long nodes = 0;
     for (int k = 1; k < p->levels; ++k) nodes += p->lv[k].np;
@@ -596,7 +636,9 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
   p->stencil_groups = 1;
   while (p->stencil_groups < 4 && p->stencil_blocks * 4 * p->stencil_groups < 152L * 24)
     p->stencil_groups *= 2;
-  const int sm = (int)p->stencil_smem;
+  // the limit is a property of the kernel, shared by every plan in the
+  // process: set it to the budget ceiling, not to this plan's tile size
+  const int sm = (int)kStencilSmemMax;
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if (cudaFuncSetAttribute(k_stencil<T, true, 1>, attr, sm) != cudaSuccess ||
       cudaFuncSetAttribute(k_stencil<T, false, 1>, attr, sm) != cudaSuccess ||

@@ -18,6 +18,8 @@ constexpr int kScanTile = 2048;   // cells per block in the cell-count scan
 constexpr int kStencilTile = 8;   // output tile edge of the level-stencil kernel
 constexpr int kStencilThreads = 128;
 constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
+constexpr size_t kStencilSmemMax = 200 * 1024;  // dynamic shared memory of a stencil tile
+constexpr int kPairSplitMax = 8;  // lanes per atom of the pair kernel: 1, 2, 4 or 8
 
 // 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
@@ -70,6 +72,8 @@ struct Plan {
   size_t stencil_smem = 0;
   bool stencil_global = false;  // tile does not fit in shared memory
   int stencil_groups = 1;       // thread groups (of 128) sharing one tile
+  bool stencil_tc = false;      // tensor-core stencil (mixed precision)
+  uint32_t* d_tcw = nullptr;    // its packed split weight pairs
   // coarsest level tables
   std::vector<double> h_top_T, h_top_V;
 
@@ -84,6 +88,8 @@ struct Plan {
   int pair_split = 1;          // lanes per atom in the pair kernel
   void* d_e0 = nullptr;        // T[N] local potential (sorted order)
   void* d_floc = nullptr;      // T[3N] local forces (sorted order)
+  void* d_q1fx = nullptr;      // int32 (FP32 modes) / int64 (FP64) fixed-point anterpolation sums
+  void* d_bmax = nullptr;      // T[N/256]: largest |c| per binning block
   void* d_q[kMaxLevels + 1] = {};
   void* d_e[kMaxLevels + 1] = {};
   void* d_et[kMaxLevels + 1] = {};
@@ -94,9 +100,13 @@ struct Plan {
   double* d_epart = nullptr;   // energy partials (interpolation blocks)
   double* d_wpart = nullptr;   // virial partials: pair blocks | stencil blocks | top nodes
   long n_epart = 0, n_wpart = 0, n_pair_blocks = 0;
-  long wpart_stencil = 0, wpart_top = 0;  // offsets (in 6-double records)
+  // virial partials, in 6-double records: stencil blocks | coarsest nodes |
+  // pair blocks (room for the largest lane split; only the records of the
+  // current split are written and summed)
+  long wpart_stencil = 0, wpart_top = 0, wpart_pair = 0;
   double* d_out = nullptr;     // [0] energy, [1..6] virial
-  int* d_flag = nullptr;       // device error flags
+  int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] scan ticket,
+                               // [3] max cell population, [4..5] max |c| (double bits)
   double* h_out = nullptr;     // pinned host staging of d_out
 
   // per-stage event timing (mls6_profile): start/end event per stage
@@ -134,6 +144,12 @@ double dg_level_over_r(int k, int l, double a, double r);
 int eval_launch(Plan* p, const void* pos, const void* c, void* forces, double* energy,
                 double* virial, double* atom_energy);
 int upload_tables(Plan* p);
+int plan_streams(Plan* p);  // create the plan's internal streams and events
+// Enqueue one evaluation on the plan's internal streams (cs, cs2), no
+// ordering against the caller's stream; energy/virial written to device
+// pointers if given.  Returns kernels launched or a negative status.
+int enqueue_eval(Plan* p, const void* pos, const void* c, void* forces, double* energy_dev,
+                 double* virial_dev, bool vir, bool capturing);
 
 // kernel launchers; each returns the number of kernels it launched
 template <typename T> int launch_bin(Plan* p, const T* pos, const T* c, cudaStream_t st);
@@ -148,5 +164,17 @@ int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_
 template <typename T> int prepare_grid_kernels(Plan* p);
 int launch_reduce(Plan* p, bool vir, cudaStream_t st);
 int pair_split(long N);  // lanes per atom of the pair kernel (mls6_pair.cu)
+// virial partial records summed by the final reduction
+inline long wpart_used(const Plan* p) {
+  return p->wpart_pair + (p->N > 0 ? (p->N * p->pair_split + kBlock - 1) / kBlock : 0);
+}
+bool stencil_fuses_top(const Plan* p);
+// tensor-core stencil (mls6_stencil_tc.cu)
+size_t tc_smem_bytes(int P);
+bool stencil_tc_eligible(const Plan* p);
+void tc_geometry(Plan* p);
+std::vector<uint32_t> tc_weight_table(const Plan* p);
+int prepare_stencil_tc(Plan* p);
+int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st);
 
 }  // namespace mls6

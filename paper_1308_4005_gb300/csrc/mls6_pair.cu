@@ -3,6 +3,7 @@
 //   W   += 1/2 c_i sum c_j g_0'(r)/r d (x) d,       d = x_j - x_i + n L,
 // with g_0 = r^-6 - a^-6 gamma(r/a); gamma is an even polynomial in r so no
 // square root is taken and each pair costs one reciprocal.
+#include <algorithm>
 #include <cmath>
 
 #include "mls6_device.cuh"
@@ -13,9 +14,10 @@ static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 template <typename T> struct PairArgs {
   Box3<T> box;
-  T inv_w[3];
+  T w[3], inv_w[3];
   int nc[3], R[3];
   T a2, ia2, ia6, ia8;
+  T margin;  // absolute slack of the row trimming (covers rounding of x, x/w)
 };
 
 template <typename T> __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
@@ -27,6 +29,11 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdiv
 // to the S lanes, and the lanes' partial sums are combined by shuffles.
 // S > 1 raises the number of resident warps for small systems, where one
 // lane per atom leaves the SMs waiting on memory latency.
+// Each row is trimmed to the cutoff sphere before its candidates are read:
+// a row whose y-z distance d from the atom is >= a is skipped, otherwise
+// only the cells within sqrt(a^2 - d^2) in x are scanned.  The trimming is
+// conservative (a small slack); the exact test r^2 < a^2 stays per pair, so
+// it changes which candidates are read, never the result.
 template <typename T, bool VIR, int S>
 __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
@@ -52,13 +59,23 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
       const T sz = (T)((z - iz) / g.nc[2]) * g.box.L[2];
       const int y = cy + dy, iy = wrapi(y, g.nc[1]);
       const T sy = (T)((y - iy) / g.nc[1]) * g.box.L[1];
+      // distance in y and z from the atom to this (unwrapped) row of cells
+      const T ylo = (T)y * g.w[1], zlo = (T)z * g.w[2];
+      const T dyl = max(T(0), max(ylo - pi.y, pi.y - (ylo + g.w[1])) - g.margin);
+      const T dzl = max(T(0), max(zlo - pi.z, pi.z - (zlo + g.w[2])) - g.margin);
+      const T d2 = dyl * dyl + dzl * dzl;
+      if (d2 >= g.a2) continue;
+      const T rx = sqrt(g.a2 - d2) + g.margin;
+      const int xlo = max(-g.R[0], (int)floor((pi.x - rx) * g.inv_w[0]) - cx);
+      const int xhi = min(g.R[0], (int)floor((pi.x + rx) * g.inv_w[0]) - cx);
+      const T py = pi.y - sy, pz = pi.z - sz;
       const int row = g.nc[0] * (iy + g.nc[1] * iz);
-      int dx = -g.R[0];
-      while (dx <= g.R[0]) {
+      int dx = xlo;
+      while (dx <= xhi) {
         const int x = cx + dx, ix = wrapi(x, g.nc[0]);
         const int wx = (x - ix) / g.nc[0];
-        const int last = min(g.R[0], dx + (g.nc[0] - 1 - ix));  // same image run
-        const T sx = (T)wx * g.box.L[0];
+        const int last = min(xhi, dx + (g.nc[0] - 1 - ix));  // same image run
+        const T px = pi.x - (T)wx * g.box.L[0];
         const bool same = (wx == 0) && (y == iy) && (z == iz);
         const int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
         // candidates four at a time: the four loads are issued together;
@@ -69,8 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
           for (int u = 0; u < 4; ++u) pj[u] = sp[min(j + u, j1 - 1)];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const T ddx = (pj[u].x - pi.x) + sx, ddy = (pj[u].y - pi.y) + sy,
-                    ddz = (pj[u].z - pi.z) + sz;
+            const T ddx = pj[u].x - px, ddy = pj[u].y - py, ddz = pj[u].z - pz;
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
             const bool valid = (j + u < j1) && !(same && j + u == i);
             if (valid && r2 < g.a2) {
@@ -114,11 +130,12 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
     floc[3 * (size_t)i + 2] = -ci * fz;
   }
   if (VIR) {
-    const double hc = 0.5 * (double)ci;
-    double wv[6] = {hc * w0, hc * w1, hc * w2, hc * w3, hc * w4, hc * w5};
-    block_sum_n<6>(wv, sh);
+    // lanes of one atom hold disjoint candidate sets: all contribute
+    T wv[6] = {ci * w0, ci * w1, ci * w2, ci * w3, ci * w4, ci * w5};
+    double ws[6];
+    block_sum_lo<T, 6>(wv, ws, sh);
     if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = wv[c];
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * ws[c];
   }
 }
 
@@ -137,10 +154,12 @@ static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, cudaStream_t st) 
   const long nb = cdiv((long)N * S, kBlock);
   if (vir)
     k_pair<T, true, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
-                                              pg, (T*)p->d_e0, (T*)p->d_floc, p->d_wpart);
+                                              pg, (T*)p->d_e0, (T*)p->d_floc,
+                                              p->d_wpart + 6 * p->wpart_pair);
   else
     k_pair<T, false, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
-                                               pg, (T*)p->d_e0, (T*)p->d_floc, p->d_wpart);
+                                               pg, (T*)p->d_e0, (T*)p->d_floc,
+                                               p->d_wpart + 6 * p->wpart_pair);
 }
 
 template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
@@ -148,10 +167,16 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
   for (int d = 0; d < 3; ++d) {
     pg.box.L[d] = (T)p->L[d];
     pg.box.invL[d] = (T)(1.0 / p->L[d]);
+    pg.w[d] = (T)p->cg.w[d];
     pg.inv_w[d] = (T)p->cg.inv_w[d];
     pg.nc[d] = p->cg.nc[d];
     pg.R[d] = p->cg.R[d];
   }
+  // slack: 1e-3 of a cell plus 16 rounding units of the largest coordinate
+  const double eps = p->prec == MLS6_FP64 ? 1.1e-16 : 6.0e-8;
+  const double wmin = std::min(p->cg.w[0], std::min(p->cg.w[1], p->cg.w[2]));
+  const double lmax = std::max(p->L[0], std::max(p->L[1], p->L[2]));
+  pg.margin = (T)(1e-3 * wmin + 16.0 * eps * lmax);
   pg.a2 = (T)(p->a * p->a);
   pg.ia2 = (T)(1.0 / (p->a * p->a));
   pg.ia6 = (T)std::pow(p->a, -6.0);

@@ -236,7 +236,8 @@ static void free_plan(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_pos_w, p->d_cell_of, p->d_cell_count, p->d_cell_start, p->d_sorted,
                   p->d_sorted_idx, p->d_e0, p->d_floc, p->d_rows, p->d_wv, p->d_top_T,
-                  p->d_top_V, p->d_epart, p->d_wpart, p->d_out, p->d_flag, p->d_scan};
+                  p->d_top_V, p->d_epart, p->d_wpart, p->d_out, p->d_flag, p->d_scan,
+                  p->d_q1fx, p->d_tcw, p->d_bmax};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 1; k <= kMaxLevels; ++k) {
@@ -279,13 +280,33 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
   return MLS6_OK;
 }
 
+int mls6_auto_levels(const double box[3], double h) {
+  if (!box) return MLS6_ERR_ARG;
+  int n1[3];
+  int rc = grid_dims_impl(box, h, 1, n1);
+  if (rc) return rc;
+  int best = 1;
+  for (int l = 2; l <= kMaxLevels; ++l) {
+    if (grid_dims_impl(box, h, l, n1)) break;
+    const int c = std::min(n1[0], std::min(n1[1], n1[2])) >> (l - 1);
+    if (c < 4) break;
+    best = l;
+  }
+  return best;
+}
+
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision) {
   if (!out) return MLS6_ERR_ARG;
   *out = nullptr;
   if (!box || N < 0 || N > (int64_t)1 << 30 || !(a > 0.0) || !std::isfinite(a)) return MLS6_ERR_ARG;
-  if (precision != MLS6_FP64 && precision != MLS6_FP32) return MLS6_ERR_ARG;
+  if (precision != MLS6_FP64 && precision != MLS6_FP32 && precision != MLS6_MIXED)
+    return MLS6_ERR_ARG;
   if (order != 3) return MLS6_ERR_ORDER;
+  if (levels == 0) {
+    levels = mls6_auto_levels(box, h);
+    if (levels < 0) return levels;
+  }
   int n1[3];
   int rc = grid_dims_impl(box, h, levels, n1);
   if (rc) return rc;
@@ -407,6 +428,40 @@ int mls6_plan_info(const mls6_plan_t* plan, int* n_grid, double* h_actual, int* 
     for (int d = 0; d < 3; ++d) h_actual[d] = p->lv[1].h[d];
   if (levels) *levels = p->levels;
   if (ntaps) *ntaps = p->ntaps;
+  return MLS6_OK;
+}
+
+int mls6_set_tuning(mls6_plan_t* plan, int split, int groups) {
+  if (!plan) return MLS6_ERR_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8) return MLS6_ERR_ARG;
+  if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return MLS6_ERR_ARG;
+  const int s2 = split ? split : p->pair_split;
+  const int g2 = (groups && !p->stencil_global) ? groups : p->stencil_groups;
+  if (s2 == p->pair_split && g2 == p->stencil_groups) return MLS6_OK;
+  if (p->cs && cudaStreamSynchronize(p->cs) != cudaSuccess) return MLS6_ERR_CUDA;
+  if (p->cs2 && cudaStreamSynchronize(p->cs2) != cudaSuccess) return MLS6_ERR_CUDA;
+  p->pair_split = s2;
+  p->stencil_groups = g2;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return MLS6_OK;
+}
+
+int mls6_stencil_kind(const mls6_plan_t* plan) {
+  if (!plan) return MLS6_ERR_ARG;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  if (p->levels < 2) return -1;
+  return p->stencil_tc ? 2 : (p->stencil_global ? 1 : 0);
+}
+
+int mls6_get_tuning(const mls6_plan_t* plan, int* split, int* groups) {
+  if (!plan) return MLS6_ERR_ARG;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  if (split) *split = p->pair_split;
+  if (groups) *groups = p->stencil_groups;
   return MLS6_OK;
 }
 

@@ -69,6 +69,53 @@ def workload(name: str) -> Workload:
     raise KeyError(name)
 
 
+def batch_workloads(B: int = 256, nmin: int = 2048, nmax: int = 65536, rho: float = 0.8,
+                    a: float = 2.5, h: float = 1.0, seed: int = SEED_BASE + 3,
+                    c6=(0.5, 1.5)) -> list:
+    """Independent replicas of uneven size (the batched workload): N drawn
+    log-uniform in [nmin, nmax]; even replicas are periodic cubes at density
+    rho, odd ones liquid slabs of the 65,536-atom slab's proportions (box
+    Lx = Ly, Lz = 3 Lx, slab 0.4267 Lz thick, centred, density rho inside).
+    Grid levels are left to the library's automatic rule (levels = 0)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(math.log(nmin), math.log(nmax), B))).astype(np.int64)
+    seeds = rng.integers(1, 2**31 - 1, B)
+    out = []
+    for r in range(B):
+        N = int(sizes[r])
+        if r % 2 == 0:
+            L = (N / rho) ** (1.0 / 3.0)
+            out.append(Workload(f"rep{r}_cube{N}", N, (L, L, L), _cube(L), tuple(c6), a, h, 0,
+                                int(seeds[r])))
+        else:
+            f = 51.2 / 120.0
+            Lx = (N / (rho * 3.0 * f)) ** (1.0 / 3.0)
+            Lz = 3.0 * Lx
+            t = f * Lz
+            z0 = 0.5 * (Lz - t)
+            out.append(Workload(f"rep{r}_slab{N}", N, (Lx, Lx, Lz),
+                                ((0.0, Lx), (0.0, Lx), (z0, z0 + t)), tuple(c6), a, h, 0,
+                                int(seeds[r])))
+    return out
+
+
+def generate_batch(ws, processes: int = 0):
+    """Concatenated (x[sum N, 3], c[sum N]) and the B+1 row offsets; replicas
+    are generated independently (in a spawned process pool if processes>1)."""
+    if processes and processes > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(processes) as pool:
+            parts = pool.map(generate, ws)
+    else:
+        parts = [generate(w) for w in ws]
+    off = np.zeros(len(ws) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([w.N for w in ws])
+    x = np.concatenate([p[0] for p in parts]) if parts else np.zeros((0, 3))
+    c = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0)
+    return x, c, off
+
+
 def scaled_cube(N: int, rho: float, a: float, h: float, levels: int, seed: int,
                 c6=(0.5, 1.5), dmin: float = 0.8) -> Workload:
     """A uniform periodic cube of N atoms at density rho."""

@@ -27,13 +27,20 @@ MLS6_ERR_SIZE = -9
 
 MLS6_FP64 = 0
 MLS6_FP32 = 1
+MLS6_MIXED = 2
+_PREC = {"fp64": MLS6_FP64, "fp32": MLS6_FP32, "mixed": MLS6_MIXED,
+         MLS6_FP64: MLS6_FP64, MLS6_FP32: MLS6_FP32, MLS6_MIXED: MLS6_MIXED}
 
 # every symbol declared in include/mls6.h
 EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream",
            "mls6_set_graph", "mls6_eval",
            "mls6_eval_atoms", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
-           "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_coarse_apply_noalloc",
-           "mls6_destroy", "mls6_status_string")
+           "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_auto_levels",
+           "mls6_set_tuning", "mls6_get_tuning", "mls6_stencil_kind", "mls6_cost_model", "mls6_lpt_assign",
+           "mls6_batch_plan", "mls6_batch_set_stream", "mls6_batch_eval", "mls6_batch_tune",
+           "mls6_batch_set_config", "mls6_batch_info", "mls6_batch_size", "mls6_batch_replica",
+           "mls6_batch_destroy",
+           "mls6_coarse_apply_noalloc", "mls6_destroy", "mls6_status_string")
 
 _lib = None
 _dp = C.POINTER(C.c_double)
@@ -90,6 +97,37 @@ def load(path: str = LIB_PATH):
     L.mls6_coarse_apply_noalloc.restype = C.c_int
     L.mls6_destroy.argtypes = [C.c_void_p]
     L.mls6_destroy.restype = None
+    L.mls6_auto_levels.argtypes = [_dp, C.c_double]
+    L.mls6_auto_levels.restype = C.c_int
+    L.mls6_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.mls6_set_tuning.restype = C.c_int
+    L.mls6_stencil_kind.argtypes = [C.c_void_p]
+    L.mls6_stencil_kind.restype = C.c_int
+    L.mls6_get_tuning.argtypes = [C.c_void_p, _ip, _ip]
+    L.mls6_get_tuning.restype = C.c_int
+    L.mls6_cost_model.argtypes = [_dp, C.c_int64, C.c_double, C.c_double, C.c_int, _dp, _dp]
+    L.mls6_cost_model.restype = C.c_int
+    L.mls6_lpt_assign.argtypes = [C.c_int, _dp, C.c_int, _ip, _dp]
+    L.mls6_lpt_assign.restype = C.c_int
+    L.mls6_batch_plan.argtypes = [C.POINTER(C.c_void_p), C.c_int, _dp, C.POINTER(C.c_int64),
+                                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]
+    L.mls6_batch_plan.restype = C.c_int
+    L.mls6_batch_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.mls6_batch_set_stream.restype = C.c_int
+    L.mls6_batch_eval.argtypes = [C.c_void_p] * 6
+    L.mls6_batch_eval.restype = C.c_int
+    L.mls6_batch_tune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, _dp]
+    L.mls6_batch_tune.restype = C.c_int
+    L.mls6_batch_set_config.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
+    L.mls6_batch_set_config.restype = C.c_int
+    L.mls6_batch_info.argtypes = [C.c_void_p, _ip, _ip, _ip, _ip, _dp, _ip, _ip]
+    L.mls6_batch_info.restype = C.c_int
+    L.mls6_batch_size.argtypes = [C.c_void_p, _ip, C.POINTER(C.c_int64)]
+    L.mls6_batch_size.restype = C.c_int
+    L.mls6_batch_replica.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+    L.mls6_batch_replica.restype = C.c_int
+    L.mls6_batch_destroy.argtypes = [C.c_void_p]
+    L.mls6_batch_destroy.restype = None
     L.mls6_status_string.argtypes = [C.c_int]
     L.mls6_status_string.restype = C.c_char_p
     _lib = L
@@ -174,7 +212,8 @@ def mls6_plan_info(plan):
     h = (C.c_double * 3)()
     _check(L.mls6_plan_info(C.c_void_p(plan), ng, h, None, None), "mls6_plan_info")
     dims = [tuple(ng[3 * k: 3 * k + 3]) for k in range(lev.value)]
-    return dict(levels=lev.value, n_grid=dims, h=tuple(h), ntaps=nt.value)
+    return dict(levels=lev.value, n_grid=dims, h=tuple(h), ntaps=nt.value,
+                stencil_kind=L.mls6_stencil_kind(C.c_void_p(plan)))
 
 
 def mls6_debug_grid(plan, level, which):
@@ -213,6 +252,111 @@ def mls6_destroy(plan):
         load().mls6_destroy(C.c_void_p(plan))
 
 
+def mls6_auto_levels(box, h):
+    rc = load().mls6_auto_levels(_darr(box), h)
+    if rc < 0:
+        _check(rc, "mls6_auto_levels")
+    return rc
+
+
+def mls6_set_tuning(plan, pair_split=0, stencil_groups=0):
+    _check(load().mls6_set_tuning(C.c_void_p(plan), pair_split, stencil_groups),
+           "mls6_set_tuning")
+
+
+def mls6_stencil_kind(plan):
+    return load().mls6_stencil_kind(C.c_void_p(plan))
+
+
+def mls6_get_tuning(plan):
+    s, g = C.c_int(), C.c_int()
+    _check(load().mls6_get_tuning(C.c_void_p(plan), C.byref(s), C.byref(g)), "mls6_get_tuning")
+    return s.value, g.value
+
+
+def mls6_cost_model(box, N, a, h, levels, coef=None):
+    out = C.c_double()
+    cf = _darr(coef) if coef is not None else None
+    _check(load().mls6_cost_model(_darr(box), int(N), a, h, levels, cf, C.byref(out)),
+           "mls6_cost_model")
+    return out.value
+
+
+def mls6_lpt_assign(cost, K):
+    B = len(cost)
+    br = (C.c_int * max(B, 1))()
+    load_ = (C.c_double * K)()
+    _check(load().mls6_lpt_assign(B, _darr(cost) if B else None, K, br, load_),
+           "mls6_lpt_assign")
+    return list(br)[:B], list(load_)
+
+
+def mls6_batch_plan(boxes, N, a, h, levels=0, order=3, precision=MLS6_FP64):
+    B = len(N)
+    flat = [float(v) for b in boxes for v in b]
+    handle = C.c_void_p()
+    n64 = (C.c_int64 * B)(*[int(n) for n in N])
+    _check(load().mls6_batch_plan(C.byref(handle), B, _darr(flat), n64, a, h, levels, order,
+                                  precision), "mls6_batch_plan")
+    return handle.value
+
+
+def mls6_batch_set_stream(batch, stream_handle):
+    _check(load().mls6_batch_set_stream(C.c_void_p(batch), C.c_void_p(stream_handle)),
+           "mls6_batch_set_stream")
+
+
+def mls6_batch_eval(batch, pos_ptr, c_ptr, forces_ptr, energy_ptr, virial_ptr):
+    return load().mls6_batch_eval(C.c_void_p(batch), C.c_void_p(pos_ptr), C.c_void_p(c_ptr),
+                                  C.c_void_p(forces_ptr), C.c_void_p(energy_ptr),
+                                  C.c_void_p(virial_ptr))
+
+
+def mls6_batch_tune(batch, pos_ptr, c_ptr, forces_ptr, reps=5):
+    best = C.c_double()
+    _check(load().mls6_batch_tune(C.c_void_p(batch), C.c_void_p(pos_ptr), C.c_void_p(c_ptr),
+                                  C.c_void_p(forces_ptr), reps, C.byref(best)),
+           "mls6_batch_tune")
+    return best.value
+
+
+def mls6_batch_set_config(batch, branches=0, pair_split=None, stencil_groups=None):
+    sp = (C.c_int * len(pair_split))(*pair_split) if pair_split is not None else None
+    sg = (C.c_int * len(stencil_groups))(*stencil_groups) if stencil_groups is not None else None
+    _check(load().mls6_batch_set_config(C.c_void_p(batch), branches, sp, sg),
+           "mls6_batch_set_config")
+
+
+def mls6_batch_size(batch):
+    B = C.c_int()
+    _check(load().mls6_batch_size(C.c_void_p(batch), C.byref(B), None), "mls6_batch_size")
+    off = (C.c_int64 * (B.value + 1))()
+    _check(load().mls6_batch_size(C.c_void_p(batch), None, off), "mls6_batch_size")
+    return B.value, list(off)
+
+
+def mls6_batch_info(batch):
+    B, _ = mls6_batch_size(batch)
+    K, nl = C.c_int(), C.c_int()
+    sp, sg, br, lv = ((C.c_int * B)() for _ in range(4))
+    cost = (C.c_double * B)()
+    _check(load().mls6_batch_info(C.c_void_p(batch), C.byref(K), sp, sg, br, cost, lv,
+                                  C.byref(nl)), "mls6_batch_info")
+    return dict(branches=K.value, pair_split=list(sp), stencil_groups=list(sg),
+                branch_of=list(br), cost=list(cost), levels=list(lv), launches=nl.value)
+
+
+def mls6_batch_replica(batch, r):
+    h = C.c_void_p()
+    _check(load().mls6_batch_replica(C.c_void_p(batch), r, C.byref(h)), "mls6_batch_replica")
+    return h.value
+
+
+def mls6_batch_destroy(batch):
+    if batch:
+        load().mls6_batch_destroy(C.c_void_p(batch))
+
+
 class Plan:
     """Owns one ``mls6_plan_t``; evaluates torch CUDA tensors in place.
 
@@ -222,7 +366,7 @@ class Plan:
     """
 
     def __init__(self, box, N, a, h, levels, precision="fp64", order=3, stream=None):
-        self.precision = MLS6_FP64 if precision in ("fp64", MLS6_FP64) else MLS6_FP32
+        self.precision = _PREC[precision]
         self.handle = mls6_plan(box, N, a, h, levels, order, self.precision)
         self.N = int(N)
         self.box = tuple(float(v) for v in box)
@@ -262,6 +406,60 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             mls6_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one ``mls6_batch_t``: B replicas evaluated by one graph launch.
+
+    ``evaluate(pos, c=None)`` takes the concatenated (sum N, 4) or (sum N, 3)
+    CUDA tensor and returns energies (B,), virials (B, 6) and forces
+    (sum N, 3); ``offsets`` gives each replica's first row.
+    """
+
+    def __init__(self, boxes, N, a, h, levels=0, precision="fp64", order=3):
+        self.precision = _PREC[precision]
+        self.handle = mls6_batch_plan(boxes, N, a, h, levels, order, self.precision)
+        self.B, self.offsets = mls6_batch_size(self.handle)
+
+    @property
+    def dtype(self):
+        import torch
+
+        return torch.float64 if self.precision == MLS6_FP64 else torch.float32
+
+    def info(self):
+        return mls6_batch_info(self.handle)
+
+    def tune(self, pos, c=None, reps=5):
+        import torch
+
+        F = torch.empty((self.offsets[-1], 3), dtype=self.dtype, device=pos.device)
+        return mls6_batch_tune(self.handle, pos.data_ptr(),
+                               c.data_ptr() if c is not None else 0, F.data_ptr(), reps)
+
+    def evaluate(self, pos, c=None, virial=True, forces=None):
+        import torch
+
+        dev = pos.device
+        F = forces if forces is not None else torch.empty((self.offsets[-1], 3),
+                                                          dtype=self.dtype, device=dev)
+        E = torch.zeros(self.B, dtype=torch.float64, device=dev)
+        W = torch.zeros((self.B, 6), dtype=torch.float64, device=dev)
+        rc = mls6_batch_eval(self.handle, pos.data_ptr(), c.data_ptr() if c is not None else 0,
+                             F.data_ptr(), E.data_ptr(), W.data_ptr() if virial else 0)
+        _check(rc, "mls6_batch_eval")
+        return dict(E=E, W=W, F=F)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mls6_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

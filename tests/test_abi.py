@@ -68,7 +68,7 @@ def test_plan_argument_validation_needs_no_gpu(lib):
     assert lib.mls6_plan(C.byref(h), box, -1, 2.5, 1.0, 3, 3, 0) == mls6.MLS6_ERR_ARG
     assert lib.mls6_plan(C.byref(h), box, 100, 0.0, 1.0, 3, 3, 0) == mls6.MLS6_ERR_ARG
     assert lib.mls6_plan(C.byref(h), box, 100, 2.5, -1.0, 3, 3, 0) == mls6.MLS6_ERR_ARG
-    assert lib.mls6_plan(C.byref(h), box, 100, 2.5, 1.0, 0, 3, 0) == mls6.MLS6_ERR_GRID
+    assert lib.mls6_plan(C.byref(h), box, 100, 2.5, 1.0, -1, 3, 0) == mls6.MLS6_ERR_GRID
     assert lib.mls6_plan(C.byref(h), box, 100, 2.5, 1.0, 3, 3, 7) == mls6.MLS6_ERR_ARG
     bad = mls6._darr((10.0, -1.0, 10.0))
     assert lib.mls6_plan(C.byref(h), bad, 100, 2.5, 1.0, 3, 3, 0) == mls6.MLS6_ERR_BOX
