@@ -41,6 +41,13 @@ FLOP_TAP = 2            # one stencil tap (multiply-add) per node
 FLOP_TAP_VIR = 12       # ... plus six virial multiply-adds
 
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# it on the named workload and precision (virial on); a kernel changed since
+# its capture has no entry and reports null.
+TRAFFIC = {("slab65536", "fp32", "pair"): 1.191424e6,
+           ("cube1m", "fp32", "stencil"): 6.509568e6,
+           ("cube1m", "fp32", "pair"): None}
+
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}
 
@@ -54,6 +61,8 @@ def parse():
     ap.add_argument("--workload", default="slab65536")
     ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-virial", action="store_true",
+                    help="evaluate energy and forces only (no virial arithmetic)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workloads: keep the seeded configuration")
     ap.add_argument("--dwell", type=float, default=1.5,
@@ -344,6 +353,7 @@ def I_auto_levels(w):
 def config_of(w, args, world):
     return {"workload": w.name, "N_per_gpu": w.N, "box": list(w.box), "a": w.a, "h": w.h,
             "levels": w.levels, "order": 3, "precision": args.precision,
+            "virial": not getattr(args, "no_virial", False),
             "parallelism": f"replicas{world}" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -382,9 +392,11 @@ def run_ours(args):
         pos.copy_(pos_h, non_blocking=True)
     stream.synchronize()
 
+    vir_ptr = 0 if args.no_virial else out.data_ptr() + 8
+
     def step():
         rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), out.data_ptr(),
-                            out.data_ptr() + 8)
+                            vir_ptr)
         if rc:
             raise mls6.MLS6Error(rc, "mls6_eval")
 
@@ -470,12 +482,14 @@ def run_ours(args):
     nodes_lt = sum(n[0] * n[1] * n[2] for n in lv[:-1])
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    fp_pair = FLOP_PAIR + (0 if args.no_virial else FLOP_PAIR_VIR)
+    fp_tap = FLOP_TAP + (0 if args.no_virial else FLOP_TAP_VIR)
     work = {
-        "pair": ("alu", n_pairs * (FLOP_PAIR + FLOP_PAIR_VIR) / 1e12, "TFLOP/s",
-                 f"{n_pairs} ordered pairs inside a x {FLOP_PAIR + FLOP_PAIR_VIR} flop"),
-        "stencil": ("alu", nodes_lt * info["ntaps"] * (FLOP_TAP + FLOP_TAP_VIR) / 1e12,
+        "pair": ("alu", n_pairs * fp_pair / 1e12, "TFLOP/s",
+                 f"{n_pairs} ordered pairs inside a x {fp_pair} flop"),
+        "stencil": ("alu", nodes_lt * info["ntaps"] * fp_tap / 1e12,
                     "TFLOP/s", f"{nodes_lt} nodes on levels < l x {info['ntaps']} taps x "
-                               f"{FLOP_TAP + FLOP_TAP_VIR} flop"),
+                               f"{fp_tap} flop"),
         "interpolate": ("hbm", (N * (16 + 4 + esz + 3 * esz + 3 * esz) + lv[0][0] * lv[0][1] *
                                 lv[0][2] * esz) / 1e9, "GB/s",
                         "per atom: sorted record, index, e0, local force in, force out; grid once"),
@@ -501,8 +515,9 @@ def run_ours(args):
                                           "(median sampled SM clock)")
         else:
             peak, peak_note = hbm_peak(), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+        traffic = None if args.no_virial else TRAFFIC.get((w.name, args.precision, dom))
         roof = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                "frac": ach / peak, "traffic": None, "work": note, "peak_source": peak_note,
+                "frac": ach / peak, "traffic": traffic, "work": note, "peak_source": peak_note,
                 "avg_launch_ms": stage_ms[dom],
                 "timing": ("CUDA events on the launching stream around the stage, averaged over "
                            "a serialised pass of the same steps right after the timed region")}

@@ -273,6 +273,70 @@ int mls6_batch_size(const mls6_batch_t* b, int* B, int64_t* offsets);
 /* Release the batch, its plans and all their device memory.  NULL is ignored. */
 void mls6_batch_destroy(mls6_batch_t* b);
 
+/* ---------------------------------------------------------------------
+ * Learned force correction for a coarse grid.  The paper has no
+ * counterpart: a small network reads each atom's neighbourhood of the
+ * level-1 total potential e^{1,tot} of a (coarse) evaluation and predicts
+ * the force residual to a finer evaluation; forces += c_i * s * y_i.  The
+ * plain evaluation is unchanged and remains the reference.
+ *
+ * Features (per atom, input order, 128 per row): for the 27 offsets d in
+ * {-1,0,1}^3 (x fastest) the potential and its gradient (4 values)
+ * interpolated with the method's basis (Eq. interpolation) at x_i + h_1 d,
+ * then sin and cos of 2 pi times the fractional level-1 grid coordinate of
+ * x_i per axis, zero padding; each normalised as (f - shift_j) * scale_j.
+ * Network: 128 -> 64 -> 64 -> 64 -> 8 (outputs 0..2 used), tanh hidden
+ * layers, BF16 weights and activations on the tensor cores with FP32
+ * accumulation.  Parameters: one FP32 vector of mls6_mlp_n_params() values,
+ * W1 (128 x 64, row = input) b1 W2 (64 x 64) b2 W3 b3 W4 (64 x 8) b4.
+ * Training: loss (1/N) sum_i sum_{c<3} (y_ic - t_ic)^2, FP32 gradient with
+ * fixed-order reductions (reproducible), Adam (0.9, 0.999, 1e-8).
+ * All calls are asynchronous on the model's stream (mls6_mlp_set_stream)
+ * except where a host result is returned; calls that take a plan run on the
+ * plan's stream.
+ * --------------------------------------------------------------------- */
+typedef struct mls6_mlp_t mls6_mlp_t;
+
+int mls6_mlp_n_params(void);
+
+/* New model: Glorot-uniform weights drawn from SplitMix64(seed), zero
+ * biases, identity normalisation, output scale 1. */
+int mls6_mlp_create(mls6_mlp_t** out, uint64_t seed);
+int mls6_mlp_set_stream(mls6_mlp_t* m, void* stream);
+
+/* Parameters to / from host memory (n must equal mls6_mlp_n_params());
+ * setting them resets the optimiser state. */
+int mls6_mlp_get_params(const mls6_mlp_t* m, float* host, int n);
+int mls6_mlp_set_params(mls6_mlp_t* m, const float* host, int n);
+
+/* Feature normalisation (host arrays of 128) and output scale s. */
+int mls6_mlp_set_norm(mls6_mlp_t* m, const float* shift, const float* scale, float out_scale);
+
+/* Normalised features of the plan's last evaluation, written to the device
+ * array out (N x 128, fmt 0 = bf16, 1 = float), input order. */
+int mls6_mlp_features(mls6_plan_t* p, const mls6_mlp_t* m, void* out, int fmt);
+
+/* Network outputs Y (device, N x 8 floats) for features X (device, N x 128
+ * bf16). */
+int mls6_mlp_forward(mls6_mlp_t* m, const void* X, int64_t N, float* Y);
+
+/* Gradient of the loss for targets T (device, N x 3 floats) into grad
+ * (device, n_params floats; may be NULL) and the loss (host, may be NULL:
+ * a host loss makes the call wait). */
+int mls6_mlp_grad(mls6_mlp_t* m, const void* X, const float* T, int64_t N, float* grad,
+                  double* loss);
+
+/* One Adam step on the batch (X, T) with learning rate lr. */
+int mls6_mlp_train_step(mls6_mlp_t* m, const void* X, const float* T, int64_t N, float lr,
+                        double* loss);
+
+/* Correct the forces of the plan's last evaluation in place (device, N x 3
+ * of the plan precision, input order): features, network, then
+ * F_i += c_i * s * y_i.  Three kernels on the plan's stream. */
+int mls6_mlp_apply(mls6_plan_t* p, mls6_mlp_t* m, void* forces);
+
+void mls6_mlp_destroy(mls6_mlp_t* m);
+
 /* Coarsest-level product that allocates no device memory.  The paper has no
  * counterpart: this is a library convenience for callers that may not
  * allocate device memory when they call in -- an MD engine that reserves

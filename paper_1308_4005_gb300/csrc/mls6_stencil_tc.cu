@@ -20,8 +20,9 @@
 // fragments from packed weight pairs (5 words per part and channel cover
 // both k-steps) and runs, per line group, two ldmatrix.x4 (hi, lo) and six
 // mma.  The virial uses three more weight channels (G, G dx, G dx^2) whose
-// products with the line group are dotted with the centre values q_mu and
-// folded per row as in the FP32 kernel (Sec. II.B; strain derivative).
+// products with the line group (weights split, q_hi only: four mma) are
+// dotted with the centre values q_mu and folded per row as in the FP32
+// kernel (Sec. II.B; strain derivative).
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string.h>
@@ -103,6 +104,18 @@ __device__ __forceinline__ void toeplitz_mma(float (&d)[4], const Frag5& h, cons
   mma16816(d, l.p[1], l.p[0], l.p[2], l.p[1], bh[0], bh[1]);
   mma16816(d, h.p[3], h.p[2], h.p[4], h.p[3], bh[2], bh[3]);
   mma16816(d, h.p[3], h.p[2], h.p[4], h.p[3], bl[2], bl[3]);
+  mma16816(d, l.p[3], l.p[2], l.p[4], l.p[3], bh[2], bh[3]);
+}
+
+// Virial channels: D += T * B_hi with T split (A_hi + A_lo), two products.
+// The dropped T * B_lo term is a per-node relative error <= 2^-9 of q in a
+// sum over all nodes (the virial is a global bilinear form), where it
+// averages out; the weights stay exact to 2^-18.
+__device__ __forceinline__ void toeplitz_mma2(float (&d)[4], const Frag5& h, const Frag5& l,
+                                              const uint32_t (&bh)[4]) {
+  mma16816(d, h.p[1], h.p[0], h.p[2], h.p[1], bh[0], bh[1]);
+  mma16816(d, l.p[1], l.p[0], l.p[2], l.p[1], bh[0], bh[1]);
+  mma16816(d, h.p[3], h.p[2], h.p[4], h.p[3], bh[2], bh[3]);
   mma16816(d, l.p[3], l.p[2], l.p[4], l.p[3], bh[2], bh[3]);
 }
 
@@ -200,13 +213,13 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_stencil_tc(TcArgs A, double* 
       toeplitz_mma(acc[j], h0, l0, bh, bl);
       if (VIR) {
         float u[4] = {0.f, 0.f, 0.f, 0.f};
-        toeplitz_mma(u, h1, l1, bh, bl);
+        toeplitz_mma2(u, h1, l1, bh);
         t0 += u[0] * qmu[j][0] + u[1] * qmu[j][1] + u[2] * qmu[j][2] + u[3] * qmu[j][3];
         float v[4] = {0.f, 0.f, 0.f, 0.f};
-        toeplitz_mma(v, h2, l2, bh, bl);
+        toeplitz_mma2(v, h2, l2, bh);
         t1 += v[0] * qmu[j][0] + v[1] * qmu[j][1] + v[2] * qmu[j][2] + v[3] * qmu[j][3];
         float s[4] = {0.f, 0.f, 0.f, 0.f};
-        toeplitz_mma(s, h3, l3, bh, bl);
+        toeplitz_mma2(s, h3, l3, bh);
         t2 += s[0] * qmu[j][0] + s[1] * qmu[j][1] + s[2] * qmu[j][2] + s[3] * qmu[j][3];
       }
     }

@@ -40,6 +40,9 @@ EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream
            "mls6_batch_plan", "mls6_batch_set_stream", "mls6_batch_eval", "mls6_batch_tune",
            "mls6_batch_set_config", "mls6_batch_info", "mls6_batch_size", "mls6_batch_replica",
            "mls6_batch_destroy",
+           "mls6_mlp_n_params", "mls6_mlp_create", "mls6_mlp_set_stream", "mls6_mlp_get_params",
+           "mls6_mlp_set_params", "mls6_mlp_set_norm", "mls6_mlp_features", "mls6_mlp_forward",
+           "mls6_mlp_grad", "mls6_mlp_train_step", "mls6_mlp_apply", "mls6_mlp_destroy",
            "mls6_coarse_apply_noalloc", "mls6_destroy", "mls6_status_string")
 
 _lib = None
@@ -126,6 +129,26 @@ def load(path: str = LIB_PATH):
     L.mls6_batch_size.restype = C.c_int
     L.mls6_batch_replica.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
     L.mls6_batch_replica.restype = C.c_int
+    _fp = C.POINTER(C.c_float)
+    L.mls6_mlp_n_params.argtypes = []
+    L.mls6_mlp_n_params.restype = C.c_int
+    L.mls6_mlp_create.argtypes = [C.POINTER(C.c_void_p), C.c_uint64]
+    L.mls6_mlp_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.mls6_mlp_get_params.argtypes = [C.c_void_p, _fp, C.c_int]
+    L.mls6_mlp_set_params.argtypes = [C.c_void_p, _fp, C.c_int]
+    L.mls6_mlp_set_norm.argtypes = [C.c_void_p, _fp, _fp, C.c_float]
+    L.mls6_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.mls6_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    L.mls6_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, _dp]
+    L.mls6_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                      _dp]
+    L.mls6_mlp_apply.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    for fn in ("mls6_mlp_create", "mls6_mlp_set_stream", "mls6_mlp_get_params",
+               "mls6_mlp_set_params", "mls6_mlp_set_norm", "mls6_mlp_features",
+               "mls6_mlp_forward", "mls6_mlp_grad", "mls6_mlp_train_step", "mls6_mlp_apply"):
+        getattr(L, fn).restype = C.c_int
+    L.mls6_mlp_destroy.argtypes = [C.c_void_p]
+    L.mls6_mlp_destroy.restype = None
     L.mls6_batch_destroy.argtypes = [C.c_void_p]
     L.mls6_batch_destroy.restype = None
     L.mls6_status_string.argtypes = [C.c_int]
@@ -460,6 +483,98 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             mls6_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """Owns one ``mls6_mlp_t`` (learned force correction; see mls6.h)."""
+
+    def __init__(self, seed=0):
+        L = load()
+        h = C.c_void_p()
+        _check(L.mls6_mlp_create(C.byref(h), seed), "mls6_mlp_create")
+        self.handle = h.value
+        self.n_params = L.mls6_mlp_n_params()
+
+    def set_stream(self, stream_handle):
+        _check(load().mls6_mlp_set_stream(C.c_void_p(self.handle), C.c_void_p(stream_handle)),
+               "mls6_mlp_set_stream")
+
+    def get_params(self):
+        import numpy as np
+
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().mls6_mlp_get_params(C.c_void_p(self.handle),
+                                          out.ctypes.data_as(C.POINTER(C.c_float)),
+                                          self.n_params), "mls6_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        _check(load().mls6_mlp_set_params(C.c_void_p(self.handle),
+                                          p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+               "mls6_mlp_set_params")
+
+    def set_norm(self, shift, scale, out_scale):
+        import numpy as np
+
+        sh = np.ascontiguousarray(np.asarray(shift, dtype=np.float32))
+        sc = np.ascontiguousarray(np.asarray(scale, dtype=np.float32))
+        fp = C.POINTER(C.c_float)
+        _check(load().mls6_mlp_set_norm(C.c_void_p(self.handle), sh.ctypes.data_as(fp),
+                                        sc.ctypes.data_as(fp), float(out_scale)),
+               "mls6_mlp_set_norm")
+
+    def features(self, plan, fmt="bf16"):
+        import torch
+
+        dt = torch.bfloat16 if fmt == "bf16" else torch.float32
+        out = torch.empty((plan.N, 128), dtype=dt, device="cuda")
+        _check(load().mls6_mlp_features(C.c_void_p(plan.handle), C.c_void_p(self.handle),
+                                        C.c_void_p(out.data_ptr()), 0 if fmt == "bf16" else 1),
+               "mls6_mlp_features")
+        return out
+
+    def forward(self, X):
+        import torch
+
+        Y = torch.empty((X.shape[0], 8), dtype=torch.float32, device=X.device)
+        _check(load().mls6_mlp_forward(C.c_void_p(self.handle), C.c_void_p(X.data_ptr()),
+                                       X.shape[0], C.c_void_p(Y.data_ptr())), "mls6_mlp_forward")
+        return Y
+
+    def grad(self, X, T):
+        import torch
+
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = C.c_double()
+        _check(load().mls6_mlp_grad(C.c_void_p(self.handle), C.c_void_p(X.data_ptr()),
+                                    C.c_void_p(T.data_ptr()), X.shape[0],
+                                    C.c_void_p(g.data_ptr()), C.byref(loss)), "mls6_mlp_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        loss = C.c_double()
+        _check(load().mls6_mlp_train_step(C.c_void_p(self.handle), C.c_void_p(X.data_ptr()),
+                                          C.c_void_p(T.data_ptr()), X.shape[0], float(lr),
+                                          C.byref(loss)), "mls6_mlp_train_step")
+        return loss.value
+
+    def apply(self, plan, forces):
+        _check(load().mls6_mlp_apply(C.c_void_p(plan.handle), C.c_void_p(self.handle),
+                                     C.c_void_p(forces.data_ptr())), "mls6_mlp_apply")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mls6_mlp_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

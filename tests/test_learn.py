@@ -1,0 +1,175 @@
+"""Learned force correction.
+
+CPU (pins of the FP64 reference in oracle/mlp.py):
+  - the analytic gradient equals central finite differences of the loss;
+  - the features reproduce a quadratic field exactly (the cubic basis of the
+    method reproduces polynomials of degree <= 2), gradients included.
+GPU (through the C-ABI):
+  - features of an FP64 plan equal the reference features built from the
+    oracle's e^{1,tot} grid (stored as float: 1e-6 of the largest entry);
+  - the BF16 tensor-core forward pass and the gradient match the FP64
+    reference within BF16 precision (activations rounded to 8 bits and
+    tanh.approx: 3e-2 of the output RMS, 5e-2 relative L2 for the gradient);
+  - training lowers the loss; the trained correction lowers the force error
+    of a coarse grid on a held-out system.
+"""
+import numpy as np
+import pytest
+
+from paper_1308_4005_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def mlp_ref(orc):
+    from oracle import mlp
+
+    return mlp
+
+
+def test_mlp_reference_gradient_fd(mlp_ref):
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 0.2, mlp_ref.n_params())
+    # outputs 3..7 are unused (their weights stay zero)
+    for W, b in [mlp_ref.unpack(p)[3]]:
+        W[:, 3:] = 0.0
+        b[3:] = 0.0
+    X = rng.normal(0, 1, (7, 128))
+    T = rng.normal(0, 1, (7, 3))
+    loss, g = mlp_ref.loss_grad(p, X, T)
+    idx = rng.choice(p.size, 60, replace=False)
+    idx = np.r_[idx, [0, 8191, 8192, 12352, 16576, 17088, 17090]]
+    for j in idx:
+        e = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[j] += e
+        pm[j] -= e
+        fd = (mlp_ref.loss_grad(pp, X, T)[0] - mlp_ref.loss_grad(pm, X, T)[0]) / (2 * e)
+        assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(fd)), (j, fd, g[j])
+
+
+def test_features_reproduce_quadratic_field(mlp_ref):
+    """E sampled from f(x) = a + b.x + x^T Q x on the nodes (no wrap near the
+    atoms): the 27 interpolated values and gradients equal f and grad f."""
+    n = (24, 20, 22)
+    h = np.array([0.7, 0.8, 0.9])
+    rng = np.random.default_rng(5)
+    a0 = 0.3
+    b = rng.normal(size=3)
+    Q = rng.normal(size=(3, 3))
+    Q = Q + Q.T
+    zz, yy, xx = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    P = np.stack([xx * h[0], yy * h[1], zz * h[2]], axis=-1)
+    E = a0 + P @ b + np.einsum("...i,ij,...j->...", P, Q, P)
+    x = np.array([[8.1, 7.3, 9.9], [6.4, 8.8, 7.05], [9.95, 6.5, 8.6]])
+    Fe = mlp_ref.features(E, h, x)
+    for i in range(x.shape[0]):
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    k = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+                    p = x[i] + h * np.array([dx, dy, dz])
+                    f = a0 + p @ b + p @ Q @ p
+                    gf = b + 2 * Q @ p
+                    assert Fe[i, 4 * k] == pytest.approx(f, rel=1e-12, abs=1e-11)
+                    assert np.allclose(Fe[i, 4 * k + 1:4 * k + 4], gf, rtol=1e-11, atol=1e-11)
+        t = x[i] / h - np.floor(x[i] / h)
+        assert np.allclose(Fe[i, 108:114:2], np.sin(2 * np.pi * t))
+        assert np.allclose(Fe[i, 109:114:2], np.cos(2 * np.pi * t))
+        assert np.all(Fe[i, 114:] == 0)
+
+
+# ------------------------------------------------------------------- GPU
+
+
+@pytest.mark.gpu
+def test_features_vs_reference(gpu_lib, orc, mlp_ref):
+    import torch
+
+    box, a, h, l = (9.0, 10.0, 11.0), 2.5, 0.9, 2
+    x, c = I.uniform_atoms(41, 400, box)
+    plan = gpu_lib.Plan(box, len(c), a, h, l, precision="fp64")
+    pos = torch.tensor(np.c_[x, c], dtype=torch.float64, device="cuda")
+    plan.evaluate(pos, virial=False)
+    m = gpu_lib.MLP(1)
+    Xg = m.features(plan, fmt="f32").cpu().double().numpy()
+    n = orc.grid_dims(box, h, l)
+    G = orc.grids(box, a, n, l, x, c)
+    hh = np.array(box) / np.array(n)
+    xw = np.mod(x, np.array(box))
+    Xr = mlp_ref.features(G[0][2], hh, xw)
+    scale = np.abs(Xr).max()
+    assert np.abs(Xg - Xr).max() <= 1e-6 * scale
+
+
+def _rand_params(mlp_ref, seed, sd=0.15):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, sd, mlp_ref.n_params())
+    W4, b4 = mlp_ref.unpack(p)[3]
+    W4[:, 3:] = 0.0
+    b4[3:] = 0.0
+    return p
+
+
+@pytest.mark.gpu
+def test_forward_and_gradient_vs_reference(gpu_lib, mlp_ref):
+    import torch
+
+    p = _rand_params(mlp_ref, 11)
+    rng = np.random.default_rng(12)
+    N = 1000  # several 16-atom tiles, a ragged tail and two gradient chunks
+    Xb = torch.tensor(rng.normal(0, 1, (N, 128)), dtype=torch.float32).to(torch.bfloat16)
+    X64 = Xb.double().numpy()
+    T = rng.normal(0, 0.5, (N, 3))
+    m = gpu_lib.MLP(0)
+    m.set_params(p.astype(np.float32))
+    p32 = p.astype(np.float32).astype(np.float64)
+    Y = m.forward(Xb.cuda()).cpu().double().numpy()
+    Yr, _ = mlp_ref.forward(p32, X64)
+    rms = np.sqrt(np.mean(Yr[:, :3] ** 2))
+    assert np.abs(Y[:, :3] - Yr[:, :3]).max() <= 3e-2 * rms * 4
+    assert np.sqrt(np.mean((Y[:, :3] - Yr[:, :3]) ** 2)) <= 3e-2 * rms
+    assert np.all(Y[:, 3:] == 0.0)
+    loss, g = m.grad(Xb.cuda(), torch.tensor(T, dtype=torch.float32).cuda())
+    lr_, gr = mlp_ref.loss_grad(p32, X64, T)
+    assert loss == pytest.approx(lr_, rel=3e-2)
+    g = g.cpu().double().numpy()
+    assert np.linalg.norm(g - gr) <= 5e-2 * np.linalg.norm(gr)
+    # deterministic
+    loss2, g2 = m.grad(Xb.cuda(), torch.tensor(T, dtype=torch.float32).cuda())
+    assert loss2 == loss and torch.equal(g2.cpu(), torch.tensor(g, dtype=torch.float32))
+
+
+@pytest.mark.gpu
+def test_training_lowers_loss(gpu_lib, mlp_ref):
+    """A target the network can represent (a random network of the same
+    shape) is learned: the loss falls by 10x."""
+    import torch
+
+    rng = np.random.default_rng(21)
+    N = 8192
+    Xb = torch.tensor(rng.normal(0, 1, (N, 128)), dtype=torch.float32).to(torch.bfloat16)
+    pt = _rand_params(mlp_ref, 22, sd=0.12)
+    Tr, _ = mlp_ref.forward(pt, Xb.double().numpy())
+    T = torch.tensor(Tr[:, :3] / np.sqrt(np.mean(Tr[:, :3] ** 2)), dtype=torch.float32).cuda()
+    m = gpu_lib.MLP(5)
+    X = Xb.cuda()
+    l0 = m.grad(X, T)[0]
+    for s in range(400):
+        loss = m.train_step(X, T, 3e-3 if s < 300 else 1e-3)
+    assert loss < 0.1 * l0, (l0, loss)
+
+
+@pytest.mark.gpu
+def test_learned_correction_gain(gpu_lib):
+    """Trained on two slabs, evaluated on a held-out one: the correction
+    lowers eps_F of the h = 2 grid."""
+    from paper_1308_4005_gb300 import learn
+
+    st = learn.Setup()
+    train = [learn.slab_system(12000, 1000 + s) for s in range(2)]
+    model, hist = learn.build_model(st, train, steps=600, batch=8192, lr=2e-3)
+    assert hist[-1] < hist[0]
+    box, x, c = learn.slab_system(12000, 2000)
+    acc = learn.accuracy(model, st, box, x, c)
+    print("eps_F", acc)
+    assert acc["learned"] < acc["coarse"]
