@@ -724,6 +724,185 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------- throughput at equal accuracy
+
+def _timed_evals(fn, steps, warmup, stream):
+    import torch
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_accuracy(args):
+    """Force error against a converged reference and throughput of the plain
+    FP32, mixed-precision and learned forms over a cutoff sweep on a held-out
+    slab (proportions of the 4,194,304-atom slab), and the throughput of
+    each form interpolated (log-log) at eps_F = 1e-4."""
+    import numpy as np
+    import torch
+
+    from paper_1308_4005_gb300 import build as B
+    from paper_1308_4005_gb300 import learn
+    from paper_1308_4005_gb300 import mls6
+
+    world, rank, local = dist_setup(torch)
+    torch.cuda.set_device(local)
+    B.build()
+    mls6.load()
+    N = 1048576 if args.workload == "accuracy" else 65536
+    box, x, c = learn.slab_system(N, 7000 + rank)
+    stream = torch.cuda.Stream()
+    ref = learn.Setup()
+    _, _, Fref = learn._forces(box, x, c, ref.a_ref, ref.h_ref, "fp32")
+    cuts = [3.0, 3.5, 4.0] if args.workload == "accuracy" else [3.0, 3.5]
+    res = {"fp32": [], "mixed": [], "learned": []}
+    pos32 = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
+    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    for a in cuts:
+        for form in ("fp32", "mixed"):
+            plan = mls6.Plan(box, N, a, 1.0, 0, precision=form, stream=stream.cuda_stream)
+            r = plan.evaluate(pos32, virial=False)
+            torch.cuda.synchronize()
+            eps = learn.eps_F(r["F"], Fref)
+            ms = _timed_evals(lambda: mls6.mls6_eval(plan.handle, pos32.data_ptr(), 0,
+                                                     F.data_ptr(), 0, 0), 20, 3, stream)
+            res[form].append({"a": a, "h": 1.0, "eps_F": eps, "ms": ms, "value": N / (ms / 1e3)})
+            plan.close()
+        st = learn.Setup(a=a)
+        train = [learn.slab_system(32768, 9000 + 10 * int(4 * a) + s) for s in range(2)]
+        model, hist = learn.build_model(st, train, steps=800, batch=16384, lr=2e-3)
+        plan = mls6.Plan(box, N, a, st.h_coarse, 0, precision="fp32", stream=stream.cuda_stream)
+        r = plan.evaluate(pos32, virial=False)
+        torch.cuda.synchronize()  # the plan runs on its own stream
+        Fl = r["F"].clone()
+        torch.cuda.synchronize()
+        model.apply(plan, Fl)
+        torch.cuda.synchronize()
+        eps_c = learn.eps_F(r["F"], Fref)
+        eps = learn.eps_F(Fl, Fref)
+
+        def learned_step():
+            mls6.mls6_eval(plan.handle, pos32.data_ptr(), 0, F.data_ptr(), 0, 0)
+            model.apply(plan, F)
+
+        ms = _timed_evals(learned_step, 20, 3, stream)
+        res["learned"].append({"a": a, "h": st.h_coarse, "eps_F": eps, "eps_F_coarse": eps_c,
+                               "ms": ms, "value": N / (ms / 1e3), "train_loss": hist[-1]})
+        model.close()
+        plan.close()
+
+    def at(points, target=1e-4):
+        pts = sorted(points, key=lambda p: p["eps_F"])
+        le = np.log([p["eps_F"] for p in pts])
+        lv = np.log([p["value"] for p in pts])
+        t = np.log(target)
+        if len(pts) < 2:
+            return None, "one point"
+        j = int(np.clip(np.searchsorted(le, t), 1, len(pts) - 1))
+        f = (t - le[j - 1]) / (le[j] - le[j - 1])
+        how = "interpolated" if le[0] <= t <= le[-1] else "extrapolated"
+        return float(np.exp(lv[j - 1] + f * (lv[j] - lv[j - 1]))), how
+
+    at_target = {k: at(v) for k, v in res.items()}
+    line = {"metric": "atom-evals/s at eps_F = 1e-4", "value": at_target["mixed"][0],
+            "unit": "atom-evals/s", "n_gpus": world, "steps": 20, "warmup": 3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16x3", "data": "synthetic",
+            "config": {"workload": f"slab{N} (proportions of the 4,194,304-atom slab)",
+                       "reference": f"FP32 MLS a={ref.a_ref}, h={ref.h_ref}",
+                       "virial": False, "cutoffs": cuts,
+                       "learned": "coarse h=2 + network trained on h=1 targets per cutoff"},
+            "at_1e-4": {k: {"value": v[0], "how": v[1]} for k, v in at_target.items()},
+            "sweep": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_learned(args):
+    """The 4,194,304-atom slab (160 x 160 x 240, a = 3): throughput of the fine
+    evaluation (h = 1), the coarse one (h = 2) and the coarse one plus the
+    learned correction (network trained first on two 32,768-atom slabs of the
+    same proportions).  Forces only (no virial), FP32."""
+    import numpy as np
+    import torch
+
+    from paper_1308_4005_gb300 import build as B
+    from paper_1308_4005_gb300 import learn
+    from paper_1308_4005_gb300 import mls6
+
+    world, rank, local = dist_setup(torch)
+    torch.cuda.set_device(local)
+    B.build()
+    mls6.load()
+    st = learn.Setup()
+    t0 = time.time()
+    train = [learn.slab_system(32768, 9100 + s) for s in range(2)]
+    model, hist = learn.build_model(st, train, steps=800, batch=16384, lr=2e-3)
+    t_train = time.time() - t0
+    N = 4194304 if args.workload == "learned4m" else 262144
+    t0 = time.time()
+    box, x, c = learn.slab_system(N, 9200 + rank)
+    t_gen = time.time() - t0
+    stream = torch.cuda.Stream()
+    pos = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
+    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, h, learned in (("fine", st.h_fine, False), ("coarse", st.h_coarse, False),
+                             ("learned", st.h_coarse, True)):
+        plan = mls6.Plan(box, N, st.a, h, 0, precision="fp32", stream=stream.cuda_stream)
+
+        def step():
+            flush.fill_(1)
+            rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), 0, 0)
+            if rc:
+                raise mls6.MLS6Error(rc, "mls6_eval")
+            if learned:
+                model.apply(plan, F)
+
+        ev = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            stream.synchronize()
+            for _ in range(args.steps):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(2)
+                a_.record(stream)
+                rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), 0, 0)
+                if learned:
+                    model.apply(plan, F)
+                b_.record(stream)
+                ev.append((a_, b_))
+        torch.cuda.synchronize()
+        ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / len(ev)
+        out[name] = {"h": h, "ms": ms, "value": N / (ms / 1e3),
+                     "levels": plan.info()["levels"], "grid": plan.info()["n_grid"][0]}
+        plan.close()
+    line = {"metric": "atom-evals/s", "value": out["learned"]["value"], "unit": "atom-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["learned"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": f"slab{N} (160x160x240 proportions)", "a": st.a,
+                       "virial": False, "train_s": t_train, "generate_s": t_gen,
+                       "train_loss": [hist[0], hist[-1]],
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "forms": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def tensor_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -742,6 +921,10 @@ def hbm_peak():
 
 def main():
     args = parse()
+    if args.workload.startswith("accuracy"):
+        return run_accuracy(args)
+    if args.workload.startswith("learned"):
+        return run_learned(args)
     if args.workload.startswith("batch"):
         if args.impl == "reference":
             return run_reference_batch(args)

@@ -133,6 +133,26 @@ int mls6_eval(mls6_plan_t* p, const void* pos, const void* c, void* forces, doub
 int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces, double* energy,
                     double* virial, double* atom_energy);
 
+/* Lorentz-Berthelot mixing (Sec. II.D): sigma_ij = (sigma_i + sigma_j)/2,
+ * eps_ij = sqrt(eps_i eps_j), pair coefficient C_ij = 2 eps_ij sigma_ij^6, so
+ * E = -1/2 sum_i sum_{j,n}' C_ij |x_i - x_j + nL|^-6 (MLS approximation).
+ * The local part uses C_ij exactly; the grid part runs once per channel of
+ * the binomial expansion C_ij = sum_k xi_{i,k} xi_{j,6-k},
+ * xi_{i,k} = (1/8) sigma_i^k sqrt(binom(6,k) 2 eps_i) (Eq.
+ * disp-pair-pot-multilevel-LorentzBerthelot, seven instances of the
+ * method), and the interpolation pairs channel k with 6-k.
+ *   pos      device, N x 3 (plan precision), any positions
+ *   sigma    device, N (plan precision), > 0
+ *   epsilon  device, N (plan precision), >= 0
+ *   forces   device, N x 3, overwritten
+ *   energy   host or device double, or NULL
+ * No virial.  Kernels are launched one by one (no graph) on the plan's
+ * stream; a host energy makes the call wait and report MLS6_ERR_NONFINITE.
+ * With all sigma_i equal the result equals mls6_eval with
+ * c_i = sqrt(2 eps_i) sigma_i^3 (geometric mixing). */
+int mls6_eval_lb(mls6_plan_t* p, const void* pos, const void* sigma, const void* epsilon,
+                 void* forces, double* energy);
+
 /* Waits for the plan's stream and returns the first device-detected error of
  * the last evaluation (MLS6_ERR_NONFINITE) or a pending CUDA error. */
 int mls6_last_error(mls6_plan_t* p);

@@ -317,6 +317,77 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
 
 int plan_streams(Plan* p) { return ensure_streams(p); }
 
+// Lorentz-Berthelot mixing (Sec. II.D): the local part with the exact pair
+// coefficients, then the grid part once per channel m = 0..6 (anterpolation
+// of xi_m, restriction, level stencils, coarsest level, prolongation; the
+// level-1 total potential of each channel kept), and one interpolation that
+// pairs channel m with xi_{6-m}.  Launched eagerly on the plan's main stream.
+template <typename T>
+static int eval_lb_t(Plan* p, const T* pos, const T* sigma, const T* eps, T* forces,
+                     double* energy) {
+  const long N = p->N;
+  double* energy_dev = (energy && is_device_ptr(energy)) ? energy : nullptr;
+  if (N == 0) {
+    if (energy_dev) CK(cudaMemsetAsync(energy_dev, 0, sizeof(double), p->stream));
+    else if (energy) *energy = 0.0;
+    return MLS6_OK;
+  }
+  if (!pos || !sigma || !eps || !forces) return MLS6_ERR_ARG;
+  int rc = ensure_streams(p);
+  if (rc) return rc;
+  const long np1 = p->lv[1].np;
+  if (!p->d_lbw) {
+    if (cudaMalloc(&p->d_lbw, sizeof(T) * N) != cudaSuccess) return MLS6_ERR_NOMEM;
+    if (cudaMalloc(&p->d_lbpot, sizeof(T) * 7 * np1) != cudaSuccess) return MLS6_ERR_NOMEM;
+  }
+  cudaStream_t st = p->cs;
+  const int l = p->levels;
+  CK(cudaEventRecord(p->ev_in, p->stream));
+  CK(cudaStreamWaitEvent(st, p->ev_in, 0));
+  CK(cudaMemsetAsync(p->d_flag, 0, sizeof(int) * 8, st));
+  int nl = launch_bin<T>(p, pos, sigma, st);  // records carry sigma as the coefficient
+  nl += launch_lb_weights<T>(p, eps, st);
+  nl += launch_pair<T>(p, false, st, true);
+  for (int m = 0; m < 7; ++m) {
+    CK(cudaMemsetAsync(p->d_q1fx, 0, sizeof(T) * np1, st));
+    nl += launch_anterp<T>(p, st, m);
+    for (int k = 1; k < l; ++k) nl += launch_restrict<T>(p, k, st);
+    nl += launch_stencil<T>(p, false, st);
+    nl += launch_top<T>(p, false, st);
+    for (int k = l - 1; k >= 1; --k) nl += launch_prolong<T>(p, k, st);
+    CK(cudaMemcpyAsync((T*)p->d_lbpot + (size_t)m * np1, p->d_et[1], sizeof(T) * np1,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  nl += launch_interp_lb<T>(p, forces, st);
+  CK(cudaGetLastError());
+  p->launches = nl;
+  if (energy_dev)
+    CK(cudaMemcpyAsync(energy_dev, p->d_out, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const bool host = energy && !energy_dev;
+  if (host) {
+    CK(cudaMemcpyAsync(p->h_out, p->d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(reinterpret_cast<int*>(p->h_out + 7), p->d_flag, sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaEventRecord(p->ev_out, st));
+  CK(cudaStreamWaitEvent(p->stream, p->ev_out, 0));
+  if (host) {
+    CK(cudaStreamSynchronize(st));
+    *energy = p->h_out[0];
+    if (*reinterpret_cast<int*>(p->h_out + 7)) return MLS6_ERR_NONFINITE;
+  }
+  return MLS6_OK;
+}
+
+int eval_lb(Plan* p, const void* pos, const void* sigma, const void* eps, void* forces,
+            double* energy) {
+  if (p->prec == MLS6_FP64)
+    return eval_lb_t<double>(p, (const double*)pos, (const double*)sigma, (const double*)eps,
+                             (double*)forces, energy);
+  return eval_lb_t<float>(p, (const float*)pos, (const float*)sigma, (const float*)eps,
+                          (float*)forces, energy);
+}
+
 int enqueue_eval(Plan* p, const void* pos, const void* c, void* forces, double* energy_dev,
                  double* virial_dev, bool vir, bool capturing) {
   if (p->N > 0 && (!pos || !forces)) return MLS6_ERR_ARG;

@@ -10,6 +10,14 @@ static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------------ anterpolation
 
+// (1/8) sqrt(binom(6, k)), the Lorentz-Berthelot expansion coefficient
+// (Sec. II.D) of channel k.
+__device__ __forceinline__ double lb_coef_d(int k) {
+  const double b = (k == 0 || k == 6) ? 1.0 : (k == 1 || k == 5) ? 6.0 : (k == 2 || k == 4) ? 15.0
+                                                                                           : 20.0;
+  return 0.125 * sqrt(b);
+}
+
 // Fixed-point accumulation of the anterpolation: 32-bit integers for the
 // FP32 modes (sums kept below 2^30; resolution ~1e-6 of the largest possible
 // node sum, below FP32 rounding of the grid part), 64-bit for FP64 (below
@@ -38,9 +46,18 @@ template <> struct Fixed<double> {
 // of it (per axis; with periodic images), and those atoms lie in at most
 // `span` cells (cells meeting a box of width 4h), each holding at most
 // flag[3] atoms: bound = flag[3] * span * max|c|.
+// Lorentz-Berthelot channel m (lbm >= 0): the coefficient is
+// xi_m = lbc sigma^m sqrt(2 eps), bounded by lbc sigma_max^m (flag[4..5])
+// times the largest sqrt(2 eps) (flag[6..7]).
 template <typename T>
-__device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, double span) {
-  const double cmax = *reinterpret_cast<const double*>(flag + 4);
+__device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, double span,
+                                              int lbm = -1, double lbc = 0.0) {
+  double cmax = *reinterpret_cast<const double*>(flag + 4);
+  if (lbm >= 0) {
+    double sm = 1.0;
+    for (int k = 0; k < lbm; ++k) sm *= cmax;
+    cmax = lbc * sm * *reinterpret_cast<const double*>(flag + 6);
+  }
   const float bound = (float)((double)flag[3] * span * cmax * (1.0 + 1e-6));
   if (!(bound > 0.f)) return 0;
   int e;
@@ -57,11 +74,17 @@ __device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, doub
 template <typename T>
 __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0,
                          T ih1, T ih2, const int* __restrict__ flag, double span,
-                         typename Fixed<T>::U* __restrict__ qfx) {
+                         typename Fixed<T>::U* __restrict__ qfx, const T* __restrict__ lbw,
+                         int lbm, double lbc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span));
+  const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span, lbm, lbc));
   Vec4<T> p = sp[i];
+  if (lbm >= 0) {  // Lorentz-Berthelot channel: xi_m = lbc sigma^m sqrt(2 eps)
+    T s = T(1);
+    for (int k = 0; k < lbm; ++k) s *= p.w;
+    p.w = (T)lbc * s * lbw[i];
+  }
   T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
   T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
   int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
@@ -93,10 +116,11 @@ __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, 
 // q^1 = fixed-point sums * 2^-s in the plan's precision.
 template <typename T>
 __global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
-                             const int* __restrict__ flag, double span, T* __restrict__ q) {
+                             const int* __restrict__ flag, double span, T* __restrict__ q,
+                             int lbm, double lbc) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span));
+  const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span, lbm, lbc));
   q[i] = Fixed<T>::from_fixed((typename Fixed<T>::I)qfx[i], iscale);
 }
 
@@ -108,17 +132,58 @@ static double support_span(const Plan* p) {
   return s;
 }
 
-template <typename T> int launch_anterp(Plan* p, cudaStream_t st) {
+// lbm >= 0: Lorentz-Berthelot channel m (coefficients computed from the
+// sorted sigma and sqrt(2 eps)); -1: the atoms' own coefficients.
+double lb_coef(int m) {
+  static const double binom[7] = {1, 6, 15, 20, 15, 6, 1};
+  return m < 0 ? 0.0 : 0.125 * std::sqrt(binom[m]);
+}
+
+template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
   const double span = support_span(p);
+  const double lbc = lb_coef(lbm);
   k_anterp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
       (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), p->d_flag, span,
-      (typename Fixed<T>::U*)p->d_q1fx);
+      (typename Fixed<T>::U*)p->d_q1fx, (const T*)p->d_lbw, lbm, lbc);
   k_from_fixed<T><<<cdiv(L1.np, kBlock), kBlock, 0, st>>>(
-      (const typename Fixed<T>::U*)p->d_q1fx, L1.np, p->d_flag, span, (T*)p->d_q[1]);
+      (const typename Fixed<T>::U*)p->d_q1fx, L1.np, p->d_flag, span, (T*)p->d_q[1], lbm, lbc);
   return 2;
+}
+
+// sqrt(2 eps) of the atoms in sorted order, and its largest value
+// (flag[6..7] as a double; one atomic per block on the value's bits, which
+// order like the integers for non-negative doubles).
+template <typename T>
+__global__ void k_lb_weights(const T* __restrict__ eps, const int* __restrict__ sidx, int N,
+                             T* __restrict__ lbw, int* __restrict__ flag) {
+  __shared__ double wmax[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (i < N) {
+    const T e = eps[sidx[i]];
+    const T w = sqrt(T(2) * (e > T(0) ? e : T(0)));
+    lbw[i] = w;
+    m = (double)w;
+    if (!isfinite(m)) atomicOr(flag, 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+    atomicMax(reinterpret_cast<unsigned long long*>(flag + 6),
+              (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t st) {
+  const int N = (int)p->N;
+  k_lb_weights<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(eps, p->d_sorted_idx, N, (T*)p->d_lbw,
+                                                     p->d_flag);
+  return 1;
 }
 
 // -------------------------------------------------------------- restriction
@@ -602,6 +667,98 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   }
 }
 
+// Lorentz-Berthelot interpolation: the seven channel potentials e^{(m),tot}
+// (level 1) are combined per node with the atom's xi_{i,6-m} before the
+// basis sum (both linear): e_i = sum_m xi_{i,6-m} e^{(m)}(x_i) and
+// F_i = F_i^loc + sum_m xi_{i,6-m} grad e^{(m)}(x_i); per-atom energy
+// -1/2 (e0_i + e_i) + 1/2 c_self C_ii with C_ii = 2 eps_i sigma_i^6.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_interp_lb(
+    const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ pot,
+    long np, int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
+    const T* __restrict__ floc, const T* __restrict__ lbw, double cself, T* __restrict__ forces,
+    double* __restrict__ epart, ReduceArgs R) {
+  __shared__ double sh[32 * 7];
+  __shared__ bool last;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double ea = 0.0;
+  if (i < N) {
+    Vec4<T> p = sp[i];
+    const T sg = p.w, w = lbw[i];
+    T xi[7];
+    T s = T(1);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      xi[k] = (T)lb_coef_d(k) * s * w;
+      s *= sg;
+    }
+    T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
+    T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
+    int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
+    T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+    phi4(u0 - f0, wx, dx);
+    phi4(u1 - f1, wy, dy);
+    phi4(u2 - f2, wz, dz);
+    int ix[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ix[k] = wrapi(b0 - 1 + k, n0);
+    T acc = 0, g0 = 0, g1 = 0, g2 = 0;
+    for (int c = 0; c < 4; ++c) {
+      int z = wrapi(b2 - 1 + c, n2);
+      for (int b = 0; b < 4; ++b) {
+        int y = wrapi(b1 - 1 + b, n1);
+        const long row = (long)n0 * (y + (long)n1 * z);
+        T sx = 0, sdx = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T v = 0;
+#pragma unroll
+          for (int m = 0; m < 7; ++m) v += xi[6 - m] * pot[m * np + row + ix[a]];
+          sx += wx[a] * v;
+          sdx += dx[a] * v;
+        }
+        acc += wy[b] * wz[c] * sx;
+        g0 += wy[b] * wz[c] * sdx;
+        g1 += dy[b] * wz[c] * sx;
+        g2 += wy[b] * dz[c] * sx;
+      }
+    }
+    int o = sidx[i];
+    forces[3 * (size_t)o + 0] = floc[3 * (size_t)i + 0] + g0 * ih0;
+    forces[3 * (size_t)o + 1] = floc[3 * (size_t)i + 1] + g1 * ih1;
+    forces[3 * (size_t)o + 2] = floc[3 * (size_t)i + 2] + g2 * ih2;
+    double cii = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) cii += (double)xi[k] * (double)xi[6 - k];
+    ea = -0.5 * ((double)e0[i] + (double)acc) + 0.5 * cself * cii;
+  }
+  double s = block_sum(ea, sh);
+  if (threadIdx.x == 0) {
+    epart[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(R.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
+    if (threadIdx.x == 0) *R.ticket = 0u;
+  }
+}
+
+template <typename T> int launch_interp_lb(Plan* p, T* forces, cudaStream_t st) {
+  const Level& L1 = p->lv[1];
+  const int N = (int)p->N;
+  ReduceArgs R = {p->d_wpart, wpart_used(p), 0, p->d_out,
+                  reinterpret_cast<unsigned*>(p->d_flag + 1)};
+  k_interp_lb<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+      (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_lbpot, L1.np, L1.n[0],
+      L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]),
+      (const T*)p->d_e0, (const T*)p->d_floc, (const T*)p->d_lbw, p->c_self, forces, p->d_epart,
+      R);
+  return 1;
+}
+
 template <typename T>
 int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st) {
   const Level& L1 = p->lv[1];
@@ -651,7 +808,9 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
 }
 
 #define MLS6_INSTANTIATE(T)                                               \
-  template int launch_anterp<T>(Plan*, cudaStream_t);                     \
+  template int launch_anterp<T>(Plan*, cudaStream_t, int);                \
+  template int launch_lb_weights<T>(Plan*, const T*, cudaStream_t);       \
+  template int launch_interp_lb<T>(Plan*, T*, cudaStream_t);              \
   template int launch_restrict<T>(Plan*, int, cudaStream_t);              \
   template int launch_stencil<T>(Plan*, bool, cudaStream_t);              \
   template int launch_top<T>(Plan*, bool, cudaStream_t);                  \

@@ -90,6 +90,8 @@ struct Plan {
   void* d_floc = nullptr;      // T[3N] local forces (sorted order)
   void* d_q1fx = nullptr;      // int32 (FP32 modes) / int64 (FP64) fixed-point anterpolation sums
   void* d_bmax = nullptr;      // T[N/256]: largest |c| per binning block
+  void* d_lbw = nullptr;       // T[N]: sqrt(2 eps) in sorted order (Lorentz-Berthelot)
+  void* d_lbpot = nullptr;     // T[7 n_1]: level-1 total potential of each LB channel
   void* d_q[kMaxLevels + 1] = {};
   void* d_e[kMaxLevels + 1] = {};
   void* d_et[kMaxLevels + 1] = {};
@@ -106,7 +108,8 @@ struct Plan {
   long wpart_stencil = 0, wpart_top = 0, wpart_pair = 0;
   double* d_out = nullptr;     // [0] energy, [1..6] virial
   int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] scan ticket,
-                               // [3] max cell population, [4..5] max |c| (double bits)
+                               // [3] max cell population, [4..5] max |c| (double),
+                               // [6..7] max sqrt(2 eps) (double, Lorentz-Berthelot)
   double* h_out = nullptr;     // pinned host staging of d_out
 
   // per-stage event timing (mls6_profile): start/end event per stage
@@ -145,6 +148,8 @@ int eval_launch(Plan* p, const void* pos, const void* c, void* forces, double* e
                 double* virial, double* atom_energy);
 int upload_tables(Plan* p);
 int plan_streams(Plan* p);  // create the plan's internal streams and events
+int eval_lb(Plan* p, const void* pos, const void* sigma, const void* eps, void* forces,
+            double* energy);
 // Enqueue one evaluation on the plan's internal streams (cs, cs2), no
 // ordering against the caller's stream; energy/virial written to device
 // pointers if given.  Returns kernels launched or a negative status.
@@ -153,8 +158,10 @@ int enqueue_eval(Plan* p, const void* pos, const void* c, void* forces, double* 
 
 // kernel launchers; each returns the number of kernels it launched
 template <typename T> int launch_bin(Plan* p, const T* pos, const T* c, cudaStream_t st);
-template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st);
-template <typename T> int launch_anterp(Plan* p, cudaStream_t st);
+template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb = false);
+template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm = -1);
+template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t st);
+template <typename T> int launch_interp_lb(Plan* p, T* forces, cudaStream_t st);
 template <typename T> int launch_restrict(Plan* p, int k, cudaStream_t st);
 template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st);
 template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st);

@@ -95,91 +95,113 @@ __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1
 
 // One thread per (atom, dz): the 9 offsets (dx, dy) of one dz.  Separable:
 // per z row of the basis, an x pass over the 6 y rows of the 6x6 node
-// block, then a y pass, then the z weights.
+// block, then a y pass, then the z weights.  A block (3 x kFA threads)
+// assembles the rows of kFA atoms in shared memory and writes each row with
+// 16-byte stores (a row per atom in input order, or in sorted order when
+// sorted_out is set).
+constexpr int kFA = 64;
+
 template <typename T>
-__global__ void k_features(const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N,
-                           const T* __restrict__ E, int n0, int n1, int n2, T ih0, T ih1, T ih2,
-                           const float* __restrict__ norm, void* __restrict__ out, int f32) {
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = (int)(gid / 3), dz = (int)(gid % 3) - 1;
-  if (i >= N) return;
-  const Vec4<T> p = sp[i];
-  const T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
-  const T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
-  const int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
-  T wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-  phi4(u0 - f0, wx, dwx);
-  phi4(u1 - f1, wy, dwy);
-  phi4(u2 - f2, wz, dwz);
-  T e[9], gx[9], gy[9], gz[9];
+__global__ void __launch_bounds__(3 * kFA) k_features(
+    const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ E,
+    int n0, int n1, int n2, T ih0, T ih1, T ih2, const float* __restrict__ norm,
+    void* __restrict__ out, int f32, int sorted_out) {
+  __shared__ __align__(16) float rows[kFA][kNF];
+  const int la = threadIdx.x / 3, dz = (int)(threadIdx.x % 3) - 1;
+  const int i = blockIdx.x * kFA + la;
+  if (i < N) {
+    const Vec4<T> p = sp[i];
+    const T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
+    const T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
+    const int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
+    T wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+    phi4(u0 - f0, wx, dwx);
+    phi4(u1 - f1, wy, dwy);
+    phi4(u2 - f2, wz, dwz);
+    T e[9], gx[9], gy[9], gz[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) e[k] = gx[k] = gy[k] = gz[k] = T(0);
-  for (int c = 0; c < 4; ++c) {
-    const int iz = wrapi(b2 + dz - 1 + c, n2);
-    // x pass: rows y = b1-2 .. b1+3, offsets dx = -1..1
-    T ax[6][3], bx[6][3];
+    for (int k = 0; k < 9; ++k) e[k] = gx[k] = gy[k] = gz[k] = T(0);
+    for (int c = 0; c < 4; ++c) {
+      const int iz = wrapi(b2 + dz - 1 + c, n2);
+      // x pass: rows y = b1-2 .. b1+3, offsets dx = -1..1
+      T ax[6][3], bx[6][3];
 #pragma unroll
-    for (int yy = 0; yy < 6; ++yy) {
-      const T* row = E + (long)n0 * (wrapi(b1 - 2 + yy, n1) + (long)n1 * iz);
-      T v[6];
+      for (int yy = 0; yy < 6; ++yy) {
+        const T* row = E + (long)n0 * (wrapi(b1 - 2 + yy, n1) + (long)n1 * iz);
+        T v[6];
 #pragma unroll
-      for (int xx = 0; xx < 6; ++xx) v[xx] = row[wrapi(b0 - 2 + xx, n0)];
+        for (int xx = 0; xx < 6; ++xx) v[xx] = row[wrapi(b0 - 2 + xx, n0)];
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        T s = 0, ds = 0;
+        for (int dx = 0; dx < 3; ++dx) {
+          T s = 0, ds = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          s += wx[a] * v[dx + a];
-          ds += dwx[a] * v[dx + a];
+          for (int a = 0; a < 4; ++a) {
+            s += wx[a] * v[dx + a];
+            ds += dwx[a] * v[dx + a];
+          }
+          ax[yy][dx] = s;
+          bx[yy][dx] = ds;
         }
-        ax[yy][dx] = s;
-        bx[yy][dx] = ds;
       }
-    }
-    // y pass and z weights
+      // y pass and z weights
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        T aa = 0, ab = 0, ba = 0;
+        for (int dx = 0; dx < 3; ++dx) {
+          T aa = 0, ab = 0, ba = 0;
 #pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-          aa += wy[bb] * ax[dy + bb][dx];
-          ab += dwy[bb] * ax[dy + bb][dx];
-          ba += wy[bb] * bx[dy + bb][dx];
+          for (int bb = 0; bb < 4; ++bb) {
+            aa += wy[bb] * ax[dy + bb][dx];
+            ab += dwy[bb] * ax[dy + bb][dx];
+            ba += wy[bb] * bx[dy + bb][dx];
+          }
+          const int k = dx + 3 * dy;
+          e[k] += wz[c] * aa;
+          gz[k] += dwz[c] * aa;
+          gy[k] += wz[c] * ab;
+          gx[k] += wz[c] * ba;
         }
-        const int k = dx + 3 * dy;
-        e[k] += wz[c] * aa;
-        gz[k] += dwz[c] * aa;
-        gy[k] += wz[c] * ab;
-        gx[k] += wz[c] * ba;
-      }
-  }
-  const long row = (long)sidx[i] * kNF;
-  auto put = [&](int j, float v) {
-    const float z = (v - norm[j]) * norm[kNF + j];
-    if (f32)
-      reinterpret_cast<float*>(out)[row + j] = z;
-    else
-      reinterpret_cast<__nv_bfloat16*>(out)[row + j] = __float2bfloat16_rn(z);
-  };
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int idx = k + 9 * (dz + 1);
-    put(4 * idx + 0, (float)e[k]);
-    put(4 * idx + 1, (float)(gx[k] * ih0));
-    put(4 * idx + 2, (float)(gy[k] * ih1));
-    put(4 * idx + 3, (float)(gz[k] * ih2));
-  }
-  if (dz == 0) {
-    const float t[3] = {(float)(u0 - f0), (float)(u1 - f1), (float)(u2 - f2)};
-    for (int d = 0; d < 3; ++d) {
-      float s, co;
-      sincospif(2.0f * t[d], &s, &co);
-      put(108 + 2 * d, s);
-      put(109 + 2 * d, co);
     }
-    for (int j = 114; j < kNF; ++j) put(j, 0.0f);
+    auto put = [&](int j, float v) { rows[la][j] = (v - norm[j]) * norm[kNF + j]; };
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int idx = k + 9 * (dz + 1);
+      put(4 * idx + 0, (float)e[k]);
+      put(4 * idx + 1, (float)(gx[k] * ih0));
+      put(4 * idx + 2, (float)(gy[k] * ih1));
+      put(4 * idx + 3, (float)(gz[k] * ih2));
+    }
+    if (dz == 0) {
+      const float t[3] = {(float)(u0 - f0), (float)(u1 - f1), (float)(u2 - f2)};
+      for (int d = 0; d < 3; ++d) {
+        float s, co;
+        sincospif(2.0f * t[d], &s, &co);
+        put(108 + 2 * d, s);
+        put(109 + 2 * d, co);
+      }
+      for (int j = 114; j < kNF; ++j) put(j, 0.0f);
+    }
+  }
+  __syncthreads();
+  // rows out: 16-byte chunks (8 bf16 or 4 floats)
+  const int per = f32 ? kNF / 4 : kNF / 8;
+  for (int t = threadIdx.x; t < kFA * per; t += blockDim.x) {
+    const int a = t / per, ch = t % per;
+    const int ii = blockIdx.x * kFA + a;
+    if (ii >= N) continue;
+    const long r = sorted_out ? ii : sidx[ii];
+    if (f32) {
+      const float4 v = *reinterpret_cast<const float4*>(&rows[a][4 * ch]);
+      reinterpret_cast<float4*>(out)[r * (kNF / 4) + ch] = v;
+    } else {
+      const float* f = &rows[a][8 * ch];
+      uint4 v;
+      v.x = pack_bf16(f[0], f[1]);
+      v.y = pack_bf16(f[2], f[3]);
+      v.z = pack_bf16(f[4], f[5]);
+      v.w = pack_bf16(f[6], f[7]);
+      reinterpret_cast<uint4*>(out)[r * (kNF / 8) + ch] = v;
+    }
   }
 }
 
@@ -516,16 +538,18 @@ __global__ void k_adam(float* __restrict__ par, float* __restrict__ m, float* __
   par[p] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
 }
 
-// forces_i += c_i * s * y_i (input order; c from the plan's wrapped records)
+// forces_o += c_o * s * y_i for the atom o at sorted position i (outputs in
+// sorted order, forces in input order)
 template <typename T>
-__global__ void k_mlp_correct(const Vec4<T>* __restrict__ posw, const float* __restrict__ Y,
-                              int N, float s, T* __restrict__ F) {
+__global__ void k_mlp_correct(const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx,
+                              const float* __restrict__ Y, int N, float s, T* __restrict__ F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const T c = posw[i].w * (T)s;
-  F[3 * (size_t)i + 0] += c * (T)Y[(size_t)i * kNO + 0];
-  F[3 * (size_t)i + 1] += c * (T)Y[(size_t)i * kNO + 1];
-  F[3 * (size_t)i + 2] += c * (T)Y[(size_t)i * kNO + 2];
+  const T c = sp[i].w * (T)s;
+  const size_t o = (size_t)sidx[i];
+  F[3 * o + 0] += c * (T)Y[(size_t)i * kNO + 0];
+  F[3 * o + 1] += c * (T)Y[(size_t)i * kNO + 1];
+  F[3 * o + 2] += c * (T)Y[(size_t)i * kNO + 2];
 }
 
 // ------------------------------------------------------------------ host
@@ -617,13 +641,14 @@ static void free_mlp(Mlp* m) {
 }
 
 template <typename T>
-static int features_t(Plan* p, Mlp* m, void* out, int f32, cudaStream_t st) {
+static int features_t(Plan* p, Mlp* m, void* out, int f32, bool sorted_out, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
   if (N == 0) return MLS6_OK;
-  k_features<T><<<cdiv(3L * N, 128), 128, 0, st>>>(
+  k_features<T><<<cdiv(N, kFA), 3 * kFA, 0, st>>>(
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
-      L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), m->d_norm, out, f32);
+      L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), m->d_norm, out, f32,
+      sorted_out ? 1 : 0);
   CK(cudaGetLastError());
   return MLS6_OK;
 }
@@ -726,8 +751,8 @@ int mls6_mlp_features(mls6_plan_t* plan, const mls6_mlp_t* mm, void* out, int fm
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (p->N > 0 && !out) return MLS6_ERR_ARG;
   Mlp* m = const_cast<Mlp*>(reinterpret_cast<const Mlp*>(mm));
-  return p->prec == MLS6_FP64 ? features_t<double>(p, m, out, fmt, p->stream)
-                              : features_t<float>(p, m, out, fmt, p->stream);
+  return p->prec == MLS6_FP64 ? features_t<double>(p, m, out, fmt, false, p->stream)
+                              : features_t<float>(p, m, out, fmt, false, p->stream);
 }
 
 int mls6_mlp_forward(mls6_mlp_t* mm, const void* X, int64_t N, float* Y) {
@@ -775,17 +800,19 @@ int mls6_mlp_apply(mls6_plan_t* plan, mls6_mlp_t* mm, void* forces) {
   if (rc) return rc;
   cudaStream_t saved = m->stream;
   m->stream = p->stream;
-  rc = p->prec == MLS6_FP64 ? features_t<double>(p, m, m->d_X, 0, p->stream)
-                            : features_t<float>(p, m, m->d_X, 0, p->stream);
+  rc = p->prec == MLS6_FP64 ? features_t<double>(p, m, m->d_X, 0, true, p->stream)
+                            : features_t<float>(p, m, m->d_X, 0, true, p->stream);
   if (!rc) rc = forward(m, m->d_X, N, m->d_Y, false);
   m->stream = saved;
   if (rc) return rc;
   if (p->prec == MLS6_FP64)
     k_mlp_correct<double><<<cdiv(N, 256), 256, 0, p->stream>>>(
-        (const Vec4<double>*)p->d_pos_w, m->d_Y, (int)N, m->out_scale, (double*)forces);
+        (const Vec4<double>*)p->d_sorted, p->d_sorted_idx, m->d_Y, (int)N, m->out_scale,
+        (double*)forces);
   else
     k_mlp_correct<float><<<cdiv(N, 256), 256, 0, p->stream>>>(
-        (const Vec4<float>*)p->d_pos_w, m->d_Y, (int)N, m->out_scale, (float*)forces);
+        (const Vec4<float>*)p->d_sorted, p->d_sorted_idx, m->d_Y, (int)N, m->out_scale,
+        (float*)forces);
   CK(cudaGetLastError());
   return MLS6_OK;
 }

@@ -34,21 +34,27 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdiv
 // only the cells within sqrt(a^2 - d^2) in x are scanned.  The trimming is
 // conservative (a small slack); the exact test r^2 < a^2 stays per pair, so
 // it changes which candidates are read, never the result.
-template <typename T, bool VIR, int S>
+// LB: Lorentz-Berthelot mixing (Sec. II.D): the sorted record carries
+// sigma_i in place of c_i and lbw holds sqrt(2 eps_i) in sorted order; the
+// pair coefficient is C_ij = lbw_i lbw_j ((sigma_i + sigma_j)/2)^6, and the
+// outputs are e0_i = sum_j C_ij g_0 and F_i = -sum_j C_ij g_0'/r d.
+template <typename T, bool VIR, int S, bool LB = false>
 __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
                                                   PairArgs<T> g, T* __restrict__ e0,
                                                   T* __restrict__ floc,
-                                                  double* __restrict__ wpart) {
+                                                  double* __restrict__ wpart,
+                                                  const T* __restrict__ lbw = nullptr) {
   __shared__ double sh[32 * 6];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gid / S, sub = gid % S;
   T e = 0, fx = 0, fy = 0, fz = 0;
   T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-  T ci = 0;
+  T ci = 0, wi = 0;
   if (i < N) {
     const Vec4<T> pi = sp[i];
     ci = pi.w;
+    if (LB) wi = lbw[i];
     const int cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
     const int cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
     const int cz = min(max((int)(pi.z * g.inv_w[2]), 0), g.nc[2] - 1);
@@ -96,8 +102,13 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
               const T s5 = s3 * s2;
               const T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
               const T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
-              e += pj[u].w * g0;
-              const T cg = pj[u].w * gp;
+              T cj = pj[u].w;
+              if (LB) {
+                const T sg = T(0.5) * (ci + pj[u].w), sg3 = sg * sg * sg;
+                cj = wi * lbw[j + u] * sg3 * sg3;
+              }
+              e += cj * g0;
+              const T cg = cj * gp;
               fx += cg * ddx;
               fy += cg * ddy;
               fz += cg * ddz;
@@ -124,10 +135,11 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
     fz += __shfl_xor_sync(0xffffffffu, fz, o);
   }
   if (i < N && sub == 0) {
+    const T cf = LB ? T(1) : ci;  // LB: the coefficient is already in the sums
     e0[i] = e;
-    floc[3 * (size_t)i + 0] = -ci * fx;
-    floc[3 * (size_t)i + 1] = -ci * fy;
-    floc[3 * (size_t)i + 2] = -ci * fz;
+    floc[3 * (size_t)i + 0] = -cf * fx;
+    floc[3 * (size_t)i + 1] = -cf * fy;
+    floc[3 * (size_t)i + 2] = -cf * fz;
   }
   if (VIR) {
     // lanes of one atom hold disjoint candidate sets: all contribute
@@ -149,10 +161,14 @@ int pair_split(long N) {
 }
 
 template <typename T, int S>
-static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, cudaStream_t st) {
+static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
   const int N = (int)p->N;
   const long nb = cdiv((long)N * S, kBlock);
-  if (vir)
+  if (lb)
+    k_pair<T, false, S, true><<<nb, kBlock, 0, st>>>(
+        (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
+        p->d_wpart + 6 * p->wpart_pair, (const T*)p->d_lbw);
+  else if (vir)
     k_pair<T, true, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
                                               pg, (T*)p->d_e0, (T*)p->d_floc,
                                               p->d_wpart + 6 * p->wpart_pair);
@@ -162,7 +178,7 @@ static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, cudaStream_t st) 
                                                p->d_wpart + 6 * p->wpart_pair);
 }
 
-template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
+template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb) {
   PairArgs<T> pg;
   for (int d = 0; d < 3; ++d) {
     pg.box.L[d] = (T)p->L[d];
@@ -182,15 +198,15 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st) {
   pg.ia6 = (T)std::pow(p->a, -6.0);
   pg.ia8 = (T)std::pow(p->a, -8.0);
   switch (p->pair_split) {
-    case 8: launch_s<T, 8>(p, pg, vir, st); break;
-    case 4: launch_s<T, 4>(p, pg, vir, st); break;
-    case 2: launch_s<T, 2>(p, pg, vir, st); break;
-    default: launch_s<T, 1>(p, pg, vir, st); break;
+    case 8: launch_s<T, 8>(p, pg, vir, lb, st); break;
+    case 4: launch_s<T, 4>(p, pg, vir, lb, st); break;
+    case 2: launch_s<T, 2>(p, pg, vir, lb, st); break;
+    default: launch_s<T, 1>(p, pg, vir, lb, st); break;
   }
   return 1;
 }
 
-template int launch_pair<float>(Plan*, bool, cudaStream_t);
-template int launch_pair<double>(Plan*, bool, cudaStream_t);
+template int launch_pair<float>(Plan*, bool, cudaStream_t, bool);
+template int launch_pair<double>(Plan*, bool, cudaStream_t, bool);
 
 }  // namespace mls6

@@ -140,7 +140,9 @@ def accuracy(model: "mls6.MLP", st: Setup, box, x, c):
     import torch
 
     plan_c, pos_c, Fc = _forces(box, x, c, st.a, st.h_coarse, st.precision)
+    torch.cuda.synchronize()
     Fl = Fc.clone()
+    torch.cuda.synchronize()
     model.apply(plan_c, Fl)
     _, _, Ff = _forces(box, x, c, st.a, st.h_fine, st.precision)
     _, _, Fr = _forces(box, x, c, st.a_ref, st.h_ref, st.precision)

@@ -34,7 +34,7 @@ _PREC = {"fp64": MLS6_FP64, "fp32": MLS6_FP32, "mixed": MLS6_MIXED,
 # every symbol declared in include/mls6.h
 EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream",
            "mls6_set_graph", "mls6_eval",
-           "mls6_eval_atoms", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
+           "mls6_eval_atoms", "mls6_eval_lb", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
            "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_auto_levels",
            "mls6_set_tuning", "mls6_get_tuning", "mls6_stencil_kind", "mls6_cost_model", "mls6_lpt_assign",
            "mls6_batch_plan", "mls6_batch_set_stream", "mls6_batch_eval", "mls6_batch_tune",
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
     L.mls6_eval_atoms.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
     L.mls6_eval_atoms.restype = C.c_int
+    L.mls6_eval_lb.argtypes = [C.c_void_p] * 6
+    L.mls6_eval_lb.restype = C.c_int
     L.mls6_last_error.argtypes = [C.c_void_p]
     L.mls6_last_error.restype = C.c_int
     L.mls6_plan_info.argtypes = [C.c_void_p, _ip, _dp, _ip, _ip]
@@ -219,6 +221,12 @@ def mls6_eval_atoms(plan, pos_ptr, c_ptr, forces_ptr, energy_ptr, virial_ptr, at
                                   C.c_void_p(c_ptr or None), C.c_void_p(forces_ptr or None),
                                   C.c_void_p(energy_ptr or None), C.c_void_p(virial_ptr or None),
                                   C.c_void_p(atom_energy_ptr or None))
+
+
+def mls6_eval_lb(plan, pos_ptr, sigma_ptr, eps_ptr, forces_ptr, energy_ptr):
+    return load().mls6_eval_lb(C.c_void_p(plan), C.c_void_p(pos_ptr), C.c_void_p(sigma_ptr),
+                               C.c_void_p(eps_ptr), C.c_void_p(forces_ptr),
+                               C.c_void_p(energy_ptr))
 
 
 def mls6_last_error(plan):
