@@ -313,19 +313,24 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(const __nv_bfloat16* __restrict
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
-#pragma unroll 2
+    // all 32 fragment words of the tile's two rows first (loads in flight
+    // together), then the 64 products
+    uint32_t xa[8][4];
+#pragma unroll
     for (int ks = 0; ks < 8; ++ks) {
       const int w0 = (16 * ks + c2) >> 1, w1 = (16 * ks + 8 + c2) >> 1;
-      const uint32_t a0 = va ? __ldg(Xw + ra * (kNF / 2) + w0) : 0u;
-      const uint32_t a1 = vb ? __ldg(Xw + rb * (kNF / 2) + w0) : 0u;
-      const uint32_t a2 = va ? __ldg(Xw + ra * (kNF / 2) + w1) : 0u;
-      const uint32_t a3 = vb ? __ldg(Xw + rb * (kNF / 2) + w1) : 0u;
+      xa[ks][0] = va ? __ldg(Xw + ra * (kNF / 2) + w0) : 0u;
+      xa[ks][1] = vb ? __ldg(Xw + rb * (kNF / 2) + w0) : 0u;
+      xa[ks][2] = va ? __ldg(Xw + ra * (kNF / 2) + w1) : 0u;
+      xa[ks][3] = vb ? __ldg(Xw + rb * (kNF / 2) + w1) : 0u;
+    }
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
 #pragma unroll
       for (int nt = 0; nt < 8; ++nt) {
         const uint2 b = sw[kPk1 + (ks * 8 + nt) * 32 + lane];
-        mma16816(acc[nt], a0, a1, a2, a3, b.x, b.y);
+        mma16816(acc[nt], xa[ks][0], xa[ks][1], xa[ks][2], xa[ks][3], b.x, b.y);
       }
-    }
     uint32_t A[4][4];
     next_a(acc, sb, c2, A);
     if (STORE) store_act(Hw, ra, rb, va, vb, c2, A);

@@ -37,8 +37,11 @@ namespace mls6 {
 static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 constexpr int kTcX = 16, kTcY = 16, kTcZ = 8;
-constexpr int kTcWarps = 4;
-constexpr int kTcNG = (kTcY / 8) * kTcZ / kTcWarps;  // line groups per warp (4)
+// warps per block: 8 for the energy-only kernel (78 registers: two blocks
+// of 8 warps per SM), 4 with the virial channels (160 registers) so that the
+// A fragments of a tap row serve 4 line groups; measured on the 1M-atom
+// cube: 180 vs 238 us without the virial, 422 vs 439 us with it
+template <bool VIR> __host__ __device__ constexpr int tc_warps() { return VIR ? 4 : 8; }
 constexpr int kTcWin = 32;                            // x window
 constexpr int kTcPitch = 40;                          // bf16 per staged line (80 B)
 constexpr int kTcWords = 64;                          // packed pairs per row, part, channel
@@ -120,7 +123,10 @@ __device__ __forceinline__ void toeplitz_mma2(float (&d)[4], const Frag5& h, con
 }
 
 template <bool VIR>
-__global__ void __launch_bounds__(kTcWarps * 32) k_stencil_tc(TcArgs A, double* __restrict__ wpart) {
+__global__ void __launch_bounds__(tc_warps<VIR>() * 32) k_stencil_tc(TcArgs A,
+                                                                    double* __restrict__ wpart) {
+  constexpr int kTcWarps = tc_warps<VIR>();
+  constexpr int kTcNG = (kTcY / 8) * kTcZ / kTcWarps;  // line groups per warp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 7];
   if ((long)blockIdx.x >= A.sblocks) {  // coarsest level: one warp per node
@@ -368,11 +374,12 @@ int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st) {
   A.tV = p->d_top_V;
   A.wtop = p->d_wpart + 6 * p->wpart_top;
   double* wp = p->d_wpart + 6 * p->wpart_stencil;
-  const long nb = p->stencil_blocks + (fuse_top ? cdiv(p->lv[l].np, kTcWarps) : 0);
+  const int warps = vir ? tc_warps<true>() : tc_warps<false>();
+  const long nb = p->stencil_blocks + (fuse_top ? cdiv(p->lv[l].np, warps) : 0);
   if (vir)
-    k_stencil_tc<true><<<nb, kTcWarps * 32, p->stencil_smem, st>>>(A, wp);
+    k_stencil_tc<true><<<nb, warps * 32, p->stencil_smem, st>>>(A, wp);
   else
-    k_stencil_tc<false><<<nb, kTcWarps * 32, p->stencil_smem, st>>>(A, wp);
+    k_stencil_tc<false><<<nb, warps * 32, p->stencil_smem, st>>>(A, wp);
   return 1;
 }
 
