@@ -20,6 +20,7 @@ template <typename T>
 __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
                       BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
                       int* __restrict__ count, int* __restrict__ flag, T* __restrict__ bmax) {
+  pdl_begin();
   __shared__ T wmax[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T cabs = T(0);
@@ -68,6 +69,7 @@ template <typename T>
 __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
                              int* __restrict__ tmax, const T* __restrict__ bmax, int nbin,
                              int* __restrict__ start, int* __restrict__ flag) {
+  pdl_begin();
   __shared__ double sh[32];
   __shared__ int shm[32];
   __shared__ double shc[32];
@@ -135,6 +137,7 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
 // start[], reset count[] for use as fill counters by the scatter.
 __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ toff,
                              int* __restrict__ start) {
+  pdl_begin();
   __shared__ int wsum[32];
   constexpr int PER = kScanTile / 256;
   long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * PER;
@@ -176,6 +179,7 @@ template <typename T>
 __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
                           const int* __restrict__ start, int* __restrict__ fill,
                           Vec4<T>* __restrict__ sorted, int* __restrict__ sidx) {
+  pdl_begin();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int cell = cell_of[i];
@@ -191,6 +195,7 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
 template <typename T>
 __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
                            int* __restrict__ sidx, int* __restrict__ count) {
+  pdl_begin();
   long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncell) return;
   count[cell] = 0;
@@ -223,16 +228,16 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
   const long ntiles = cdiv(ncell, kScanTile);
   // cell counters start at zero: set at plan creation, reset by k_cellsort
   const int nbin = (int)cdiv(N, kBlock);
-  k_bin<T><<<nbin, kBlock, 0, st>>>(pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
+  launch_pdl(k_bin<T>, nbin, kBlock, 0, st, pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
                                     p->d_cell_of, p->d_cell_count, p->d_flag, (T*)p->d_bmax);
-  k_scan_tiles<T><<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_scan + ntiles,
+  launch_pdl(k_scan_tiles<T>, ntiles, kBlock, 0, st, p->d_cell_count, ncell, p->d_scan, p->d_scan + ntiles,
                                              (const T*)p->d_bmax, nbin, p->d_cell_start,
                                              p->d_flag);
-  k_scan_final<<<ntiles, kBlock, 0, st>>>(p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
-  k_scatter<T><<<cdiv(N, kBlock), kBlock, 0, st>>>((const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
+  launch_pdl(k_scan_final, ntiles, kBlock, 0, st, p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
+  launch_pdl(k_scatter<T>, cdiv(N, kBlock), kBlock, 0, st, (const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
                                                   p->d_cell_start, p->d_cell_count,
                                                   (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
-  k_cellsort<T><<<cdiv(ncell, kBlock), kBlock, 0, st>>>(
+  launch_pdl(k_cellsort<T>, cdiv(ncell, kBlock), kBlock, 0, st, 
       p->d_cell_start, ncell, (Vec4<T>*)p->d_sorted, p->d_sorted_idx, p->d_cell_count);
   return 5;
 }

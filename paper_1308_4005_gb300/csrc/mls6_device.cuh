@@ -45,6 +45,18 @@ template <typename T> __device__ __forceinline__ void phi4(T t, T w[4], T dw[4])
   dw[3] = T(-0.5) * t * (T(2) - T(3) * t);
 }
 
+// Programmatic dependent launch: every kernel of the evaluation chain lets
+// its successor be scheduled as soon as its own blocks are running
+// (launch_dependents) and, before touching memory, waits until its
+// predecessor has completed and flushed (wait).  Ordering and visibility are
+// those of plain stream order; the successor's launch overlaps the tail of
+// its predecessor.  Both are no-ops for a kernel launched without the
+// programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -154,6 +166,24 @@ __device__ __forceinline__ void coarsest_node(const T* __restrict__ q, int n0, i
       for (int k = 0; k < 6; ++k) wpart[6 * (size_t)mu + k] = hq * v[1 + k];
     }
   }
+}
+
+// Launch with the programmatic-stream-serialization attribute (see
+// pdl_begin); same semantics as kernel<<<grid, block, smem, st>>>(args...).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 }  // namespace mls6

@@ -31,12 +31,13 @@ static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 __global__ void k_reduce(const double* __restrict__ epart, long ne,
                          const double* __restrict__ wpart, long nw, int vir,
                          double* __restrict__ out) {
+  pdl_begin();
   __shared__ double sh[32 * 7];
   final_reduce(epart, ne, wpart, nw, vir, out, sh);
 }
 
 int launch_reduce(Plan* p, bool vir, cudaStream_t st) {
-  k_reduce<<<1, kBlock, 0, st>>>(p->d_epart, p->n_epart, p->d_wpart, wpart_used(p), vir ? 1 : 0,
+  launch_pdl(k_reduce, 1, kBlock, 0, st, p->d_epart, p->n_epart, p->d_wpart, wpart_used(p), vir ? 1 : 0,
                                  p->d_out);
   return 1;
 }

@@ -76,6 +76,7 @@ __global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, 
                          T ih1, T ih2, const int* __restrict__ flag, double span,
                          typename Fixed<T>::U* __restrict__ qfx, const T* __restrict__ lbw,
                          int lbm, double lbc) {
+  pdl_begin();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span, lbm, lbc));
@@ -118,6 +119,7 @@ template <typename T>
 __global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
                              const int* __restrict__ flag, double span, T* __restrict__ q,
                              int lbm, double lbc) {
+  pdl_begin();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span, lbm, lbc));
@@ -144,11 +146,11 @@ template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm) {
   const int N = (int)p->N;
   const double span = support_span(p);
   const double lbc = lb_coef(lbm);
-  k_anterp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+  launch_pdl(k_anterp<T>, cdiv(N, kBlock), kBlock, 0, st, 
       (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
       (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), p->d_flag, span,
       (typename Fixed<T>::U*)p->d_q1fx, (const T*)p->d_lbw, lbm, lbc);
-  k_from_fixed<T><<<cdiv(L1.np, kBlock), kBlock, 0, st>>>(
+  launch_pdl(k_from_fixed<T>, cdiv(L1.np, kBlock), kBlock, 0, st, 
       (const typename Fixed<T>::U*)p->d_q1fx, L1.np, p->d_flag, span, (T*)p->d_q[1], lbm, lbc);
   return 2;
 }
@@ -159,6 +161,7 @@ template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm) {
 template <typename T>
 __global__ void k_lb_weights(const T* __restrict__ eps, const int* __restrict__ sidx, int N,
                              T* __restrict__ lbw, int* __restrict__ flag) {
+  pdl_begin();
   __shared__ double wmax[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double m = 0.0;
@@ -181,7 +184,7 @@ __global__ void k_lb_weights(const T* __restrict__ eps, const int* __restrict__ 
 
 template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t st) {
   const int N = (int)p->N;
-  k_lb_weights<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(eps, p->d_sorted_idx, N, (T*)p->d_lbw,
+  launch_pdl(k_lb_weights<T>, cdiv(N, kBlock), kBlock, 0, st, eps, p->d_sorted_idx, N, (T*)p->d_lbw,
                                                      p->d_flag);
   return 1;
 }
@@ -194,6 +197,7 @@ template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t 
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
                            int c0, int c1, int c2) {
+  pdl_begin();
   long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long np = (long)c0 * c1 * c2;
   if (mu >= np) return;
@@ -217,7 +221,7 @@ __global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* 
 
 template <typename T> int launch_restrict(Plan* p, int k, cudaStream_t st) {
   const Level &F = p->lv[k], &C = p->lv[k + 1];
-  k_restrict<T><<<cdiv(C.np, kBlock), kBlock, 0, st>>>((const T*)p->d_q[k], F.n[0], F.n[1],
+  launch_pdl(k_restrict<T>, cdiv(C.np, kBlock), kBlock, 0, st, (const T*)p->d_q[k], F.n[0], F.n[1],
                                                       F.n[2], (T*)p->d_q[k + 1], C.n[0], C.n[1],
                                                       C.n[2]);
   return 1;
@@ -265,6 +269,7 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 template <typename T, bool VIR, int G>
 __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> A,
                                                                  double* __restrict__ wpart) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 7];
   __shared__ T part[(G > 1 ? G - 1 : 1) * kStencilThreads * kStencilW];
@@ -382,6 +387,7 @@ template <typename T, bool VIR>
 __global__ void __launch_bounds__(kBlock) k_stencil_global(StencilArgs<T> A,
                                                            double* __restrict__ wpart,
                                                            long nodes_total) {
+  pdl_begin();
   __shared__ double red[32 * 6];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   // level of this node (levels are concatenated)
@@ -488,9 +494,9 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
     long nodes = 0;
     for (int k = 1; k < p->levels; ++k) nodes += p->lv[k].np;
     if (vir)
-      k_stencil_global<T, true><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
+      launch_pdl(k_stencil_global<T, true>, p->stencil_blocks, kBlock, 0, st, A, wp, nodes);
     else
-      k_stencil_global<T, false><<<p->stencil_blocks, kBlock, 0, st>>>(A, wp, nodes);
+      launch_pdl(k_stencil_global<T, false>, p->stencil_blocks, kBlock, 0, st, A, wp, nodes);
     return 1;
   }
   const int warps = kStencilThreads * p->stencil_groups / 32;
@@ -498,12 +504,12 @@ template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
                   (stencil_fuses_top(p) ? cdiv(p->lv[p->levels].np, warps) : 0);
   const size_t sm = p->stencil_smem;
   switch (p->stencil_groups * 2 + (vir ? 1 : 0)) {
-    case 2 * 4 + 1: k_stencil<T, true, 4><<<nb, kStencilThreads * 4, sm, st>>>(A, wp); break;
-    case 2 * 4 + 0: k_stencil<T, false, 4><<<nb, kStencilThreads * 4, sm, st>>>(A, wp); break;
-    case 2 * 2 + 1: k_stencil<T, true, 2><<<nb, kStencilThreads * 2, sm, st>>>(A, wp); break;
-    case 2 * 2 + 0: k_stencil<T, false, 2><<<nb, kStencilThreads * 2, sm, st>>>(A, wp); break;
-    case 2 * 1 + 1: k_stencil<T, true, 1><<<nb, kStencilThreads, sm, st>>>(A, wp); break;
-    default: k_stencil<T, false, 1><<<nb, kStencilThreads, sm, st>>>(A, wp); break;
+    case 2 * 4 + 1: launch_pdl(k_stencil<T, true, 4>, nb, kStencilThreads * 4, sm, st, A, wp); break;
+    case 2 * 4 + 0: launch_pdl(k_stencil<T, false, 4>, nb, kStencilThreads * 4, sm, st, A, wp); break;
+    case 2 * 2 + 1: launch_pdl(k_stencil<T, true, 2>, nb, kStencilThreads * 2, sm, st, A, wp); break;
+    case 2 * 2 + 0: launch_pdl(k_stencil<T, false, 2>, nb, kStencilThreads * 2, sm, st, A, wp); break;
+    case 2 * 1 + 1: launch_pdl(k_stencil<T, true, 1>, nb, kStencilThreads, sm, st, A, wp); break;
+    default: launch_pdl(k_stencil<T, false, 1>, nb, kStencilThreads, sm, st, A, wp); break;
   }
   return 1;
 }
@@ -516,6 +522,7 @@ __global__ void __launch_bounds__(128) k_top(const T* __restrict__ q, int n0, in
                                              const double* __restrict__ tT,
                                              const double* __restrict__ tV, T* __restrict__ e,
                                              double* __restrict__ wpart) {
+  pdl_begin();
   const int mu = (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5);
   if (mu < n0 * n1 * n2) coarsest_node<T, VIR>(q, n0, n1, n2, tT, tV, e, wpart, mu);
 }
@@ -526,10 +533,10 @@ template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
   const Level& Lt = p->lv[l];
   double* wp = p->d_wpart + 6 * p->wpart_top;
   if (vir)
-    k_top<T, true><<<cdiv(Lt.np, 4), 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+    launch_pdl(k_top<T, true>, cdiv(Lt.np, 4), 128, 0, st, (const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
                                           p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
   else
-    k_top<T, false><<<cdiv(Lt.np, 4), 128, 0, st>>>((const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
+    launch_pdl(k_top<T, false>, cdiv(Lt.np, 4), 128, 0, st, (const T*)p->d_q[l], Lt.n[0], Lt.n[1], Lt.n[2],
                                            p->d_top_T, p->d_top_V, (T*)p->d_e[l], wp);
   return 1;
 }
@@ -541,6 +548,7 @@ template <typename T>
 __global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
                           const T* __restrict__ etc_, int c0, int c1, int c2,
                           T* __restrict__ etf) {
+  pdl_begin();
   long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long np = (long)f0 * f1 * f2;
   if (mu >= np) return;
@@ -580,7 +588,7 @@ __global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
 
 template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st) {
   const Level &F = p->lv[k], &C = p->lv[k + 1];
-  k_prolong<T><<<cdiv(F.np, kBlock), kBlock, 0, st>>>((const T*)p->d_e[k], F.n[0], F.n[1],
+  launch_pdl(k_prolong<T>, cdiv(F.np, kBlock), kBlock, 0, st, (const T*)p->d_e[k], F.n[0], F.n[1],
                                                      F.n[2], (const T*)p->d_et[k + 1], C.n[0],
                                                      C.n[1], C.n[2], (T*)p->d_et[k]);
   return 1;
@@ -607,6 +615,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, double cself, T* __restrict__ forces,
     double* __restrict__ atom_energy, double* __restrict__ epart, ReduceArgs R) {
+  pdl_begin();
   __shared__ double sh[32 * 7];
   __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -678,6 +687,7 @@ __global__ void __launch_bounds__(kBlock) k_interp_lb(
     long np, int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, const T* __restrict__ lbw, double cself, T* __restrict__ forces,
     double* __restrict__ epart, ReduceArgs R) {
+  pdl_begin();
   __shared__ double sh[32 * 7];
   __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -751,7 +761,7 @@ template <typename T> int launch_interp_lb(Plan* p, T* forces, cudaStream_t st) 
   const int N = (int)p->N;
   ReduceArgs R = {p->d_wpart, wpart_used(p), 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1)};
-  k_interp_lb<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+  launch_pdl(k_interp_lb<T>, cdiv(N, kBlock), kBlock, 0, st, 
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_lbpot, L1.np, L1.n[0],
       L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]),
       (const T*)p->d_e0, (const T*)p->d_floc, (const T*)p->d_lbw, p->c_self, forces, p->d_epart,
@@ -765,7 +775,7 @@ int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_
   const int N = (int)p->N;
   ReduceArgs R = {p->d_wpart, wpart_used(p), vir ? 1 : 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1)};
-  k_interp<T><<<cdiv(N, kBlock), kBlock, 0, st>>>(
+  launch_pdl(k_interp<T>, cdiv(N, kBlock), kBlock, 0, st, 
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
       L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,
       (const T*)p->d_floc, p->c_self, forces, atom_energy, p->d_epart, R);

@@ -125,6 +125,7 @@ __device__ __forceinline__ void toeplitz_mma2(float (&d)[4], const Frag5& h, con
 template <bool VIR>
 __global__ void __launch_bounds__(tc_warps<VIR>() * 32) k_stencil_tc(TcArgs A,
                                                                     double* __restrict__ wpart) {
+  pdl_begin();
   constexpr int kTcWarps = tc_warps<VIR>();
   constexpr int kTcNG = (kTcY / 8) * kTcZ / kTcWarps;  // line groups per warp
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,9 +378,9 @@ int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st) {
   const int warps = vir ? tc_warps<true>() : tc_warps<false>();
   const long nb = p->stencil_blocks + (fuse_top ? cdiv(p->lv[l].np, warps) : 0);
   if (vir)
-    k_stencil_tc<true><<<nb, warps * 32, p->stencil_smem, st>>>(A, wp);
+    launch_pdl(k_stencil_tc<true>, nb, warps * 32, p->stencil_smem, st, A, wp);
   else
-    k_stencil_tc<false><<<nb, warps * 32, p->stencil_smem, st>>>(A, wp);
+    launch_pdl(k_stencil_tc<false>, nb, warps * 32, p->stencil_smem, st, A, wp);
   return 1;
 }
 
