@@ -249,3 +249,29 @@ def test_batch_host_outputs_and_nonfinite(gpu_lib, small_batch):
     rc = gpu_lib.mls6_batch_eval(bt.handle, pos.data_ptr(), 0, Fd.data_ptr(),
                                  C.addressof(Eh), C.addressof(Wh))
     assert rc == 0 and np.array_equal(np.array(Eh[:]), E0)
+
+
+@pytest.mark.gpu
+def test_batch_with_empty_replica(gpu_lib):
+    """A replica without atoms gives E = W = 0 and leaves the others as
+    their single plans."""
+    boxes = [(9.0, 9.0, 9.0), (8.0, 8.0, 8.0), (10.0, 10.0, 12.0)]
+    Ns = [500, 0, 800]
+    xs, cs = [], []
+    for r, (b, n) in enumerate(zip(boxes, Ns)):
+        x, c = I.uniform_atoms(300 + r, n, b)
+        xs.append(x if n else np.zeros((0, 3)))
+        cs.append(c if n else np.zeros(0))
+    x = np.concatenate(xs)
+    c = np.concatenate(cs)
+    bt = gpu_lib.Batch(boxes, Ns, 2.5, 1.0, 0)
+    E, W, F, _ = _batch_eval(bt, x, c, "fp64")
+    assert E[1] == 0.0 and np.all(W[1] == 0.0)
+    off = bt.offsets
+    info = bt.info()
+    for r in (0, 2):
+        w = I.Workload("r", Ns[r], boxes[r], None, (0.5, 1.5), 2.5, 1.0, 0, 0)
+        sl = slice(off[r], off[r + 1])
+        e1, w1, f1, _ = _single(gpu_lib, w, x[sl], c[sl], "fp64", info["pair_split"][r],
+                                info["stencil_groups"][r])
+        assert E[r] == e1 and np.array_equal(W[r], w1) and np.array_equal(F[sl], f1)

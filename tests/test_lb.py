@@ -129,3 +129,13 @@ def test_lb_gpu_equal_sigma_and_repeatable(gpu_lib):
     Fg = r["F"].cpu().numpy()
     assert E1 == pytest.approx(Eg, rel=1e-12)
     assert np.abs(F1 - Fg).max() <= 1e-11 * np.abs(Fg).max()
+
+
+@pytest.mark.gpu
+def test_lb_no_atoms(gpu_lib):
+    import ctypes as C
+
+    plan = gpu_lib.Plan((8.0, 8.0, 8.0), 0, 2.0, 0.8, 2, precision="fp64")
+    E = C.c_double(1.0)
+    rc = gpu_lib.mls6_eval_lb(plan.handle, 0, 0, 0, 0, C.addressof(E))
+    assert rc == 0 and E.value == 0.0
