@@ -196,11 +196,16 @@ const char* mls6_stage_name(int i);
 int mls6_auto_levels(const double box[3], double h);
 
 /* Kernel shapes of a plan.  pair_split: lanes per atom of the local pair
- * kernel (1, 2, 4 or 8); stencil_groups: thread groups of 128 sharing one
+ * kernel -- 1, 2, 4 or 8 (each lane group walks its atom's neighbour cells)
+ * or 16, 32 (warp form: two or one atoms per warp share one flattened,
+ * row-trimmed candidate stream; refused with MLS6_ERR_ARG when the
+ * neighbour range spans more than two cells per side or the box has fewer
+ * than five cells along x); stencil_groups: thread groups of 128 sharing one
  * 8^3 stencil tile (1, 2 or 4; ignored when the stencil tile does not fit in
  * shared memory); 0 keeps the current value.  The defaults come from the
- * plan's size (about 48 resident warps per SM for the pair kernel, 24 for
- * the stencil).  A shape changes the order of floating-point sums (results
+ * plan's size and precision (FP32 / mixed: about 48 resident warps per SM;
+ * FP64: the warp form with one atom per warp where allowed; stencil: 24
+ * warps per SM).  A shape changes the order of floating-point sums (results
  * move at rounding level), never what is summed.  Waits for the plan's
  * streams; the next evaluation re-captures its graph. */
 int mls6_set_tuning(mls6_plan_t* p, int pair_split, int stencil_groups);

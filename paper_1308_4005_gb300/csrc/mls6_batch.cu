@@ -427,7 +427,7 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
   // seed shapes: each plan's heuristic value
   std::vector<int> s0(b->B), g0(b->B);
   for (int r = 0; r < b->B; ++r) {
-    s0[r] = pair_split(b->plans[r]->N);
+    s0[r] = pair_split(b->plans[r]);
     g0[r] = b->plans[r]->stencil_groups;
   }
   auto shaped = [&](int sb, int gb, std::vector<int>& s, std::vector<int>& g) {
@@ -435,7 +435,7 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
     g.resize(b->B);
     for (int r = 0; r < b->B; ++r) {
       int x = sb >= 0 ? s0[r] << sb : s0[r] >> -sb;
-      s[r] = std::max(1, std::min(kPairSplitMax, x));
+      s[r] = std::max(1, std::min(pair_cluster_ok(b->plans[r]) ? kPairSplitMax : 8, x));
       int y = gb >= 0 ? g0[r] << gb : g0[r] >> -gb;
       g[r] = std::max(1, std::min(4, y));
     }

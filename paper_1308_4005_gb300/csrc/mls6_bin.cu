@@ -20,7 +20,8 @@ template <typename T>
 __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
                       BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
                       int* __restrict__ count, int* __restrict__ flag, T* __restrict__ bmax) {
-  pdl_begin();
+  const long z = pdl_begin();
+  pos += z; cc += z;
   __shared__ T wmax[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T cabs = T(0);
@@ -69,7 +70,8 @@ template <typename T>
 __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
                              int* __restrict__ tmax, const T* __restrict__ bmax, int nbin,
                              int* __restrict__ start, int* __restrict__ flag) {
-  pdl_begin();
+  const long z = pdl_begin();
+  count += z; bmax += z;
   __shared__ double sh[32];
   __shared__ int shm[32];
   __shared__ double shc[32];
@@ -137,7 +139,8 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
 // start[], reset count[] for use as fill counters by the scatter.
 __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ toff,
                              int* __restrict__ start) {
-  pdl_begin();
+  const long z = pdl_begin();
+  toff += z;
   __shared__ int wsum[32];
   constexpr int PER = kScanTile / 256;
   long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * PER;
@@ -179,7 +182,8 @@ template <typename T>
 __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
                           const int* __restrict__ start, int* __restrict__ fill,
                           Vec4<T>* __restrict__ sorted, int* __restrict__ sidx) {
-  pdl_begin();
+  const long z = pdl_begin();
+  posw += z; cell_of += z; start += z;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int cell = cell_of[i];
@@ -195,7 +199,8 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
 template <typename T>
 __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
                            int* __restrict__ sidx, int* __restrict__ count) {
-  pdl_begin();
+  const long z = pdl_begin();
+  start += z;
   long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncell) return;
   count[cell] = 0;

@@ -45,16 +45,30 @@ template <typename T> __device__ __forceinline__ void phi4(T t, T w[4], T dw[4])
   dw[3] = T(-0.5) * t * (T(2) - T(3) * t);
 }
 
-// Programmatic dependent launch: every kernel of the evaluation chain lets
-// its successor be scheduled as soon as its own blocks are running
-// (launch_dependents) and, before touching memory, waits until its
-// predecessor has completed and flushed (wait).  Ordering and visibility are
-// those of plain stream order; the successor's launch overlaps the tail of
-// its predecessor.  Both are no-ops for a kernel launched without the
-// programmatic-serialization attribute.
-__device__ __forceinline__ void pdl_begin() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+// Programmatic dependent launch: every kernel of the evaluation chain first
+// waits until its predecessor has completed and flushed (wait), then lets
+// its successor be scheduled (launch_dependents), so the successor's launch
+// overlaps this kernel's work while every memory access still follows plain
+// stream order.  Triggering before the wait let whole chains of waiting
+// kernels become resident at once, and under CUDA-graph replay a kernel
+// then read a value (the fixed-point scale) that two launches earlier had
+// not yet written; with the trigger after the wait at most one kernel waits
+// ahead of the running one.  Both are no-ops for a kernel launched without
+// the programmatic-serialization attribute.
+//
+// The wait orders memory operations only for the compiler's ordinary loads:
+// a load through a `const T* __restrict__` parameter is treated as
+// invariant for the whole kernel and may be scheduled above the wait.
+// pdl_begin therefore returns a zero produced by an opaque instruction after
+// the wait; kernels add it to every such pointer (`p += z`), so no load
+// through them can be issued before the wait (the pointers stay based on
+// their restrict parameters).
+__device__ __forceinline__ long pdl_begin() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  long z;
+  asm volatile("mov.b64 %0, 0;" : "=l"(z)::"memory");
+  return z;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -31,7 +31,8 @@ static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 __global__ void k_reduce(const double* __restrict__ epart, long ne,
                          const double* __restrict__ wpart, long nw, int vir,
                          double* __restrict__ out) {
-  pdl_begin();
+  const long z = pdl_begin();
+  epart += z; wpart += z;
   __shared__ double sh[32 * 7];
   final_reduce(epart, ne, wpart, nw, vir, out, sh);
 }
@@ -69,7 +70,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_sorted_idx, sizeof(int) * N);
   rc |= A(&p->d_e0, e * N);
   rc |= A(&p->d_floc, 3 * e * N);
-  p->pair_split = pair_split(N);
+  p->pair_split = pair_split(p);
   const int l = p->levels;
   for (int k = 1; k <= l; ++k) {
     rc |= A(&p->d_q[k], e * p->lv[k].np);

@@ -1,5 +1,6 @@
 // Grid part of multilevel summation (Sec. II.B): anterpolation, restriction,
 // evaluation on every level, prolongation and interpolation.
+#include <climits>
 #include <cmath>
 
 #include "mls6_device.cuh"
@@ -71,47 +72,108 @@ __device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, doub
 // (and everything downstream) do not depend on the order in which the
 // atomics land -- results are reproducible bit for bit.  The rounding
 // (relative 2^-s, s >= ~45 in practice) is far below FP64 parity needs.
+// A block of kBlock cell-sorted atoms touches a compact box of grid nodes:
+// when that box fits in shared memory the block first sums its
+// contributions there (integer atomics on shared memory) and then adds each
+// non-zero node once to the grid, which cuts the global atomics by the
+// overlap of the atoms' 4x4x4 supports; otherwise its atoms add to the grid
+// directly.  Both paths add the same integers, so the grid does not depend
+// on the path either.
+constexpr int kAnterpBoxBytes = 24 * 1024;
+
 template <typename T>
-__global__ void k_anterp(const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0,
-                         T ih1, T ih2, const int* __restrict__ flag, double span,
-                         typename Fixed<T>::U* __restrict__ qfx, const T* __restrict__ lbw,
-                         int lbm, double lbc) {
-  pdl_begin();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__global__ void __launch_bounds__(kBlock) k_anterp(
+    const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0, T ih1, T ih2,
+    const int* __restrict__ flag, double span, typename Fixed<T>::U* __restrict__ qfx,
+    const T* __restrict__ lbw, int lbm, double lbc) {
+  using U = typename Fixed<T>::U;
+  constexpr int kCap = kAnterpBoxBytes / (int)sizeof(U);
+  __shared__ U box[kCap];
+  __shared__ int lo[3], hi[3];
+  const long z = pdl_begin();
+  sp += z;
+  flag += z;
+  lbw += z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < N;
+  if (threadIdx.x < 3) {
+    lo[threadIdx.x] = INT_MAX;
+    hi[threadIdx.x] = INT_MIN;
+  }
   const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span, lbm, lbc));
-  Vec4<T> p = sp[i];
-  if (lbm >= 0) {  // Lorentz-Berthelot channel: xi_m = lbc sigma^m sqrt(2 eps)
+  Vec4<T> p = valid ? sp[i] : Vec4<T>{T(0), T(0), T(0), T(0)};
+  if (valid && lbm >= 0) {  // Lorentz-Berthelot channel: xi_m = lbc sigma^m sqrt(2 eps)
     T s = T(1);
     for (int k = 0; k < lbm; ++k) s *= p.w;
     p.w = (T)lbc * s * lbw[i];
   }
-  T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
-  T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
-  int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
-  T wx[4], wy[4], wz[4];
-  phi4w(u0 - f0, wx);
-  phi4w(u1 - f1, wy);
-  phi4w(u2 - f2, wz);
-  int ix[4], iy[4], iz[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    ix[k] = wrapi(b0 - 1 + k, n0);
-    iy[k] = wrapi(b1 - 1 + k, n1);
-    iz[k] = wrapi(b2 - 1 + k, n2);
+  const T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
+  const T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
+  const int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
+  __syncthreads();
+  if (valid) {  // bounding box of the block's supports (unwrapped node indices)
+    atomicMin(&lo[0], b0 - 1);
+    atomicMin(&lo[1], b1 - 1);
+    atomicMin(&lo[2], b2 - 1);
+    atomicMax(&hi[0], b0 + 2);
+    atomicMax(&hi[1], b1 + 2);
+    atomicMax(&hi[2], b2 + 2);
   }
+  __syncthreads();
+  const int e0 = hi[0] - lo[0] + 1, e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
+  const long vol = (long)e0 * e1 * e2;
+  const bool in_box = hi[0] >= lo[0] && vol <= kCap;  // the same for the whole block
+  if (in_box)
+    for (int t = threadIdx.x; t < (int)vol; t += blockDim.x) box[t] = 0;
+  __syncthreads();
+  if (valid) {
+    T wx[4], wy[4], wz[4];
+    phi4w(u0 - f0, wx);
+    phi4w(u1 - f1, wy);
+    phi4w(u2 - f2, wz);
+    if (in_box) {
+      const int x0 = b0 - 1 - lo[0], y0 = b1 - 1 - lo[1], z0 = b2 - 1 - lo[2];
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      T wyz = p.w * wy[b] * wz[c];
-      long rowi = (long)n0 * (iy[b] + (long)n1 * iz[c]);
+        for (int b = 0; b < 4; ++b) {
+          const T wyz = p.w * wy[b] * wz[c];
+          const int row = e0 * ((y0 + b) + e1 * (z0 + c)) + x0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const typename Fixed<T>::I v = Fixed<T>::to_fixed(wyz * wx[a], scale);
-        atomicAdd(&qfx[rowi + ix[a]], (typename Fixed<T>::U)v);
+          for (int a = 0; a < 4; ++a)
+            atomicAdd(&box[row + a], (U)Fixed<T>::to_fixed(wyz * wx[a], scale));
+        }
+    } else {
+      int ix[4], iy[4], iz[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ix[k] = wrapi(b0 - 1 + k, n0);
+        iy[k] = wrapi(b1 - 1 + k, n1);
+        iz[k] = wrapi(b2 - 1 + k, n2);
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const T wyz = p.w * wy[b] * wz[c];
+          const long rowi = (long)n0 * (iy[b] + (long)n1 * iz[c]);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            atomicAdd(&qfx[rowi + ix[a]], (U)Fixed<T>::to_fixed(wyz * wx[a], scale));
+        }
     }
+  }
+  if (in_box) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < (int)vol; t += blockDim.x) {
+      const U v = box[t];
+      if (v == 0) continue;
+      const int x = t % e0, y = (t / e0) % e1, zz = t / (e0 * e1);
+      const long node = wrapi(lo[0] + x, n0) +
+                        (long)n0 * (wrapi(lo[1] + y, n1) + (long)n1 * wrapi(lo[2] + zz, n2));
+      atomicAdd(&qfx[node], v);
+    }
+  }
 }
 
 // q^1 = fixed-point sums * 2^-s in the plan's precision.
@@ -119,7 +181,8 @@ template <typename T>
 __global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
                              const int* __restrict__ flag, double span, T* __restrict__ q,
                              int lbm, double lbc) {
-  pdl_begin();
+  const long z = pdl_begin();
+  qfx += z; flag += z;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span, lbm, lbc));
@@ -161,7 +224,8 @@ template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm) {
 template <typename T>
 __global__ void k_lb_weights(const T* __restrict__ eps, const int* __restrict__ sidx, int N,
                              T* __restrict__ lbw, int* __restrict__ flag) {
-  pdl_begin();
+  const long z = pdl_begin();
+  eps += z; sidx += z;
   __shared__ double wmax[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double m = 0.0;
@@ -197,7 +261,8 @@ template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t 
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
                            int c0, int c1, int c2) {
-  pdl_begin();
+  const long z = pdl_begin();
+  qf += z;
   long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long np = (long)c0 * c1 * c2;
   if (mu >= np) return;
@@ -522,7 +587,8 @@ __global__ void __launch_bounds__(128) k_top(const T* __restrict__ q, int n0, in
                                              const double* __restrict__ tT,
                                              const double* __restrict__ tV, T* __restrict__ e,
                                              double* __restrict__ wpart) {
-  pdl_begin();
+  const long z = pdl_begin();
+  q += z; tT += z; tV += z;
   const int mu = (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5);
   if (mu < n0 * n1 * n2) coarsest_node<T, VIR>(q, n0, n1, n2, tT, tV, e, wpart, mu);
 }
@@ -548,7 +614,8 @@ template <typename T>
 __global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
                           const T* __restrict__ etc_, int c0, int c1, int c2,
                           T* __restrict__ etf) {
-  pdl_begin();
+  const long z = pdl_begin();
+  ef += z; etc_ += z;
   long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long np = (long)f0 * f1 * f2;
   if (mu >= np) return;
@@ -615,7 +682,8 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, double cself, T* __restrict__ forces,
     double* __restrict__ atom_energy, double* __restrict__ epart, ReduceArgs R) {
-  pdl_begin();
+  const long z = pdl_begin();
+  sp += z; sidx += z; et += z; e0 += z; floc += z;
   __shared__ double sh[32 * 7];
   __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -687,7 +755,8 @@ __global__ void __launch_bounds__(kBlock) k_interp_lb(
     long np, int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, const T* __restrict__ lbw, double cself, T* __restrict__ forces,
     double* __restrict__ epart, ReduceArgs R) {
-  pdl_begin();
+  const long z = pdl_begin();
+  sp += z; sidx += z; pot += z; e0 += z; floc += z; lbw += z;
   __shared__ double sh[32 * 7];
   __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -19,7 +19,8 @@ constexpr int kStencilTile = 8;   // output tile edge of the level-stencil kerne
 constexpr int kStencilThreads = 128;
 constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
 constexpr size_t kStencilSmemMax = 200 * 1024;  // dynamic shared memory of a stencil tile
-constexpr int kPairSplitMax = 8;  // lanes per atom of the pair kernel: 1, 2, 4 or 8
+constexpr double kCellDiv = 2.0;  // cell width >= a / kCellDiv
+constexpr int kPairSplitMax = 32;  // lanes per atom of the pair kernel: 1 .. 32
 
 // 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
@@ -170,7 +171,8 @@ template <typename T>
 int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st);
 template <typename T> int prepare_grid_kernels(Plan* p);
 int launch_reduce(Plan* p, bool vir, cudaStream_t st);
-int pair_split(long N);  // lanes per atom of the pair kernel (mls6_pair.cu)
+int pair_split(const Plan* p);  // default lanes per atom of the pair kernel (mls6_pair.cu)
+bool pair_cluster_ok(const Plan* p);  // warp form usable (mls6_pair.cu)
 // virial partial records summed by the final reduction
 inline long wpart_used(const Plan* p) {
   return p->wpart_pair + (p->N > 0 ? (p->N * p->pair_split + kBlock - 1) / kBlock : 0);

@@ -4,6 +4,7 @@
 // with g_0 = r^-6 - a^-6 gamma(r/a); gamma is an even polynomial in r so no
 // square root is taken and each pair costs one reciprocal.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "mls6_device.cuh"
@@ -19,6 +20,22 @@ template <typename T> struct PairArgs {
   T a2, ia2, ia6, ia8;
   T margin;  // absolute slack of the row trimming (covers rounding of x, x/w)
 };
+
+// i = m n + iw with 0 <= iw < n: the cell iw and periodic image m of an
+// unwrapped cell index (|m| is 0 or 1 unless the box is thinner than the
+// neighbour range).
+__device__ __forceinline__ void wrap_image(int i, int n, int& iw, int& m) {
+  iw = i;
+  m = 0;
+  while (iw < 0) {
+    iw += n;
+    --m;
+  }
+  while (iw >= n) {
+    iw -= n;
+    ++m;
+  }
+}
 
 template <typename T> __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
@@ -61,10 +78,11 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
     const int ny = 2 * g.R[1] + 1, nrows = (2 * g.R[2] + 1) * ny;
     for (int r = sub; r < nrows; r += S) {
       const int dz = r / ny - g.R[2], dy = r % ny - g.R[1];
-      const int z = cz + dz, iz = wrapi(z, g.nc[2]);
-      const T sz = (T)((z - iz) / g.nc[2]) * g.box.L[2];
-      const int y = cy + dy, iy = wrapi(y, g.nc[1]);
-      const T sy = (T)((y - iy) / g.nc[1]) * g.box.L[1];
+      const int z = cz + dz, y = cy + dy;
+      int iz, iy, mz, my;
+      wrap_image(z, g.nc[2], iz, mz);
+      wrap_image(y, g.nc[1], iy, my);
+      const T sz = (T)mz * g.box.L[2], sy = (T)my * g.box.L[1];
       // distance in y and z from the atom to this (unwrapped) row of cells
       const T ylo = (T)y * g.w[1], zlo = (T)z * g.w[2];
       const T dyl = max(T(0), max(ylo - pi.y, pi.y - (ylo + g.w[1])) - g.margin);
@@ -76,13 +94,12 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
       const int xhi = min(g.R[0], (int)floor((pi.x + rx) * g.inv_w[0]) - cx);
       const T py = pi.y - sy, pz = pi.z - sz;
       const int row = g.nc[0] * (iy + g.nc[1] * iz);
-      int dx = xlo;
-      while (dx <= xhi) {
-        const int x = cx + dx, ix = wrapi(x, g.nc[0]);
-        const int wx = (x - ix) / g.nc[0];
-        const int last = min(xhi, dx + (g.nc[0] - 1 - ix));  // same image run
+      int dx = xlo, ix, wx;
+      wrap_image(cx + xlo, g.nc[0], ix, wx);
+      for (; dx <= xhi; ix = 0, ++wx) {  // runs of one image; the next starts at cell 0
+        const int last = min(xhi, dx + (g.nc[0] - 1 - ix));
         const T px = pi.x - (T)wx * g.box.L[0];
-        const bool same = (wx == 0) && (y == iy) && (z == iz);
+        const bool same = (wx | my | mz) == 0;
         const int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
         // candidates four at a time: the four loads are issued together;
         // slots past the run (or the atom itself) are never inside a
@@ -151,12 +168,251 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
   }
 }
 
-// Lanes per atom: the smallest of 1, 2, 4, 8 that gives about 48 resident
-// warps per SM on a 152-SM GPU.
-int pair_split(long N) {
+// Warp form of the pair sum (lanes per atom S = 32 / G, G = 1 or 2 atoms
+// per warp).  The G consecutive sorted atoms of a warp that share a row of
+// cells (constant cy, cz) form a segment; for each segment
+//   1. lane t sets up neighbour row t: the row is trimmed against the
+//      segment's bounding box (skipped if its y-z distance is >= a, else
+//      clipped in x to the box extent +- sqrt(a^2 - d^2)) and split into at
+//      most three same-image pieces of contiguous candidates;
+//   2. a warp scan turns the pieces into one flattened candidate stream;
+//   3. lane (slot js, atom gi) takes every S-th candidate of the stream and
+//      evaluates the pair branch-free (a miss adds zero).
+// All lanes of a warp run the same number of iterations, and the integer
+// work of the row set-up is done once per row, in parallel.  Each lane sums
+// its candidates in stream order; the S partial sums of an atom are combined
+// by a fixed shuffle tree, so the result is reproducible bit for bit.
+// Requires every R <= 2 (at most 25 rows) and nc[0] >= 2 R[0] + 1 (a row's
+// x range then spans at most three periodic pieces); pair_cluster_ok().
+template <typename T, bool VIR, int G, bool LB = false>
+__global__ void __launch_bounds__(kBlock) k_pair_warp(const Vec4<T>* __restrict__ sp,
+                                                       const int* __restrict__ start, int N,
+                                                       PairArgs<T> g, T* __restrict__ e0,
+                                                       T* __restrict__ floc,
+                                                       double* __restrict__ wpart,
+                                                       const T* __restrict__ lbw = nullptr) {
+  constexpr int S = 32 / G;
+  constexpr int kW = kBlock / 32;
+  constexpr int kP = 3 * 32;  // pieces of one segment: <= 3 per row, <= 32 rows
+  constexpr unsigned kAll = 0xffffffffu;
+  __shared__ double sh[32 * 6];
+  __shared__ int t_end[kW][kP], t_base[kW][kP], t_img[kW][kP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gi = lane % G, js = lane / G;
+  const long il = ((long)blockIdx.x * kW + wid) * G + gi;
+  const bool vi = il < N;
+  const int i = vi ? (int)il : 0;
+  T e = 0, fx = 0, fy = 0, fz = 0;
+  T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+  T ci = 0, wi = 0;
+  Vec4<T> pi = {T(0), T(0), T(0), T(0)};
+  int cx = 0, cy = 0, cz = 0, rid = INT_MAX;
+  if (vi) {
+    pi = sp[i];
+    ci = pi.w;
+    if (LB) wi = lbw[i];
+    cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
+    cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
+    cz = min(max((int)(pi.z * g.inv_w[2]), 0), g.nc[2] - 1);
+    rid = cy + g.nc[1] * cz;
+  }
+  const int ny = 2 * g.R[1] + 1, nrows = (2 * g.R[2] + 1) * ny;
+  for (int s = 0; s < G;) {
+    const int rs = __shfl_sync(kAll, rid, s);
+    if (rs == INT_MAX) break;  // the remaining atoms are past N
+    const unsigned seg = __ballot_sync(kAll, lane < G && rid == rs);
+    const bool act = (seg >> gi) & 1u;
+    // bounding box of the segment's atoms (lanes of one slot hold all G)
+    T xmn = act ? pi.x : T(INFINITY), xmx = act ? pi.x : T(-INFINITY);
+    T ymn = act ? pi.y : T(INFINITY), ymx = act ? pi.y : T(-INFINITY);
+    T zmn = act ? pi.z : T(INFINITY), zmx = act ? pi.z : T(-INFINITY);
+    int cxmn = act ? cx : INT_MAX, cxmx = act ? cx : INT_MIN;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      xmn = min(xmn, __shfl_xor_sync(kAll, xmn, o));
+      xmx = max(xmx, __shfl_xor_sync(kAll, xmx, o));
+      ymn = min(ymn, __shfl_xor_sync(kAll, ymn, o));
+      ymx = max(ymx, __shfl_xor_sync(kAll, ymx, o));
+      zmn = min(zmn, __shfl_xor_sync(kAll, zmn, o));
+      zmx = max(zmx, __shfl_xor_sync(kAll, zmx, o));
+      cxmn = min(cxmn, __shfl_xor_sync(kAll, cxmn, o));
+      cxmx = max(cxmx, __shfl_xor_sync(kAll, cxmx, o));
+    }
+    const int scy = __shfl_sync(kAll, cy, s), scz = __shfl_sync(kAll, cz, s);
+    // 1. lane t: row t of the (2R+1)^2 neighbour rows
+    int np = 0, cnt = 0;
+    int pj0[3] = {0, 0, 0}, pn[3] = {0, 0, 0}, pim[3] = {0, 0, 0};
+    if (lane < nrows) {
+      const int dz = lane / ny - g.R[2], dy = lane % ny - g.R[1];
+      const int z = scz + dz, y = scy + dy;
+      int iz, iy, mz, my;
+      wrap_image(z, g.nc[2], iz, mz);
+      wrap_image(y, g.nc[1], iy, my);
+      const T ylo = (T)y * g.w[1], zlo = (T)z * g.w[2];
+      const T dyl = max(T(0), max(ylo - ymx, ymn - (ylo + g.w[1])) - g.margin);
+      const T dzl = max(T(0), max(zlo - zmx, zmn - (zlo + g.w[2])) - g.margin);
+      const T d2 = dyl * dyl + dzl * dzl;
+      if (d2 < g.a2) {
+        const T rx = sqrt(g.a2 - d2) + g.margin;
+        const int xl = max(cxmn - g.R[0], (int)floor((xmn - rx) * g.inv_w[0]));
+        const int xh = min(cxmx + g.R[0], (int)floor((xmx + rx) * g.inv_w[0]));
+        const int row = g.nc[0] * (iy + g.nc[1] * iz);
+        // image of the row in y and z, packed with the x image per piece
+        const int img_yz = ((my + 8) << 4) | ((mz + 8) << 8);
+        int xa = xl, ix, mx;
+        wrap_image(xl, g.nc[0], ix, mx);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (xa <= xh) {
+            const int xb = min(xh, xa + (g.nc[0] - 1 - ix));
+            pj0[q] = start[row + ix];
+            pn[q] = start[row + ix + (xb - xa) + 1] - pj0[q];
+            pim[q] = img_yz | (mx + 8);
+            cnt += pn[q];
+            np = q + 1;
+            xa = xb + 1;
+            ix = 0;
+            ++mx;
+          }
+        }
+      }
+    }
+    // 2. pieces -> one stream: inclusive scans of piece and candidate counts
+    int np_inc = np, c_inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kAll, np_inc, o), b = __shfl_up_sync(kAll, c_inc, o);
+      if (lane >= o) {
+        np_inc += a;
+        c_inc += b;
+      }
+    }
+    const int total = __shfl_sync(kAll, c_inc, 31);
+    {
+      int slot = np_inc - np, cend = c_inc - cnt;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < np) {
+          cend += pn[q];
+          t_end[wid][slot] = cend;
+          t_base[wid][slot] = pj0[q] - (cend - pn[q]);
+          t_img[wid][slot] = pim[q];
+          ++slot;
+        }
+    }
+    __syncwarp();
+    // 3. every S-th candidate of the stream, two in flight per lane
+    int p = -1, pend = 0, pbase = 0;
+    T qx = 0, qy = 0, qz = 0;  // the atom's position shifted by the piece's image
+    bool same = false;         // piece in the zero image: exclude j == i
+    for (int k0 = js; k0 < total; k0 += 2 * S) {
+      int ju[2];
+      bool ok[2];
+      T sx[2], sy[2], sz[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * S;
+        ok[u] = act && k < total;
+        ju[u] = 0;
+        if (k < total) {
+          if (k >= pend) {
+            do {
+              ++p;
+              pend = t_end[wid][p];
+            } while (k >= pend);
+            pbase = t_base[wid][p];
+            const int im = t_img[wid][p];
+            const int mx = (im & 15) - 8, my = ((im >> 4) & 15) - 8, mz = ((im >> 8) & 15) - 8;
+            qx = pi.x - (T)mx * g.box.L[0];
+            qy = pi.y - (T)my * g.box.L[1];
+            qz = pi.z - (T)mz * g.box.L[2];
+            same = (mx | my | mz) == 0;
+          }
+          ju[u] = pbase + k;
+          ok[u] = ok[u] && !(same && ju[u] == i);
+        }
+        sx[u] = qx;
+        sy[u] = qy;
+        sz[u] = qz;
+      }
+      Vec4<T> pj[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) pj[u] = sp[ju[u]];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const T ddx = pj[u].x - sx[u], ddy = pj[u].y - sy[u], ddz = pj[u].z - sz[u];
+        const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const bool hit = ok[u] && r2 < g.a2;
+        const T rr = hit ? r2 : g.a2;  // a miss evaluates at r = a with weight zero
+        const T inv = rcp(rr);
+        const T inv3 = inv * inv * inv;
+        const T s1 = rr * g.ia2, s2 = s1 * s1, s3 = s2 * s1, s6 = s3 * s3;
+        const T s5 = s3 * s2;
+        const T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
+        const T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
+        T cj = pj[u].w;
+        if (LB) {
+          const T sg = T(0.5) * (ci + pj[u].w), sg3 = sg * sg * sg;
+          cj = wi * lbw[ju[u]] * sg3 * sg3;
+        }
+        cj = hit ? cj : T(0);
+        e += cj * g0;
+        const T cg = cj * gp;
+        fx += cg * ddx;
+        fy += cg * ddy;
+        fz += cg * ddz;
+        if (VIR) {
+          w0 += cg * ddx * ddx;
+          w1 += cg * ddy * ddy;
+          w2 += cg * ddz * ddz;
+          w3 += cg * ddx * ddy;
+          w4 += cg * ddx * ddz;
+          w5 += cg * ddy * ddz;
+        }
+      }
+    }
+    __syncwarp();  // the next segment rewrites the piece table
+    s += __popc(seg);
+  }
+#pragma unroll
+  for (int o = G; o < 32; o <<= 1) {
+    e += __shfl_xor_sync(kAll, e, o);
+    fx += __shfl_xor_sync(kAll, fx, o);
+    fy += __shfl_xor_sync(kAll, fy, o);
+    fz += __shfl_xor_sync(kAll, fz, o);
+  }
+  if (vi && js == 0) {
+    const T cf = LB ? T(1) : ci;
+    e0[i] = e;
+    floc[3 * (size_t)i + 0] = -cf * fx;
+    floc[3 * (size_t)i + 1] = -cf * fy;
+    floc[3 * (size_t)i + 2] = -cf * fz;
+  }
+  if (VIR) {
+    T wv[6] = {ci * w0, ci * w1, ci * w2, ci * w3, ci * w4, ci * w5};
+    double ws[6];
+    block_sum_lo<T, 6>(wv, ws, sh);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * ws[c];
+  }
+}
+
+bool pair_cluster_ok(const Plan* p) {
+  for (int d = 0; d < 3; ++d)
+    if (p->cg.R[d] > 2) return false;
+  return p->cg.nc[0] >= 2 * p->cg.R[0] + 1;
+}
+
+// Lanes per atom.  FP32 and mixed: the smallest of 1, 2, 4, 8 that gives
+// about 48 resident warps per SM on a 152-SM GPU (the per-atom kernel wins
+// where the hit arithmetic is cheap).  FP64: the warp form with one atom
+// per warp where it applies (its branch-free pair arithmetic keeps all
+// lanes busy on the slow FP64 pipe: 1.86 vs 2.22 ms on a 65,536-atom slab).
+int pair_split(const Plan* p) {
+  if (p->prec == MLS6_FP64 && pair_cluster_ok(p)) return 32;
   const long want = 152L * 48 * 32;
   int s = 1;
-  while (s < 8 && N * s < want) s *= 2;
+  while (s < 8 && p->N * s < want) s *= 2;
   return s;
 }
 
@@ -176,6 +432,24 @@ static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStre
     k_pair<T, false, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
                                                pg, (T*)p->d_e0, (T*)p->d_floc,
                                                p->d_wpart + 6 * p->wpart_pair);
+}
+
+template <typename T, int G>
+static void launch_w(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
+  const int N = (int)p->N;
+  const long nb = cdiv(cdiv(N, G), kBlock / 32);  // = cdiv(N * (32 / G), kBlock)
+  if (lb)
+    k_pair_warp<T, false, G, true><<<nb, kBlock, 0, st>>>(
+        (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
+        p->d_wpart + 6 * p->wpart_pair, (const T*)p->d_lbw);
+  else if (vir)
+    k_pair_warp<T, true, G><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted,
+                                                   p->d_cell_start, N, pg, (T*)p->d_e0,
+                                                   (T*)p->d_floc, p->d_wpart + 6 * p->wpart_pair);
+  else
+    k_pair_warp<T, false, G><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted,
+                                                    p->d_cell_start, N, pg, (T*)p->d_e0,
+                                                    (T*)p->d_floc, p->d_wpart + 6 * p->wpart_pair);
 }
 
 template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb) {
@@ -198,6 +472,8 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool l
   pg.ia6 = (T)std::pow(p->a, -6.0);
   pg.ia8 = (T)std::pow(p->a, -8.0);
   switch (p->pair_split) {
+    case 32: launch_w<T, 1>(p, pg, vir, lb, st); break;
+    case 16: launch_w<T, 2>(p, pg, vir, lb, st); break;
     case 8: launch_s<T, 8>(p, pg, vir, lb, st); break;
     case 4: launch_s<T, 4>(p, pg, vir, lb, st); break;
     case 2: launch_s<T, 2>(p, pg, vir, lb, st); break;

@@ -329,10 +329,10 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
       lv.np *= lv.n[d];
     }
   }
-  // cell list: width >= a/2, neighbour range R = ceil(a/w)
+  // cell list: width >= a/kCellDiv, neighbour range R = ceil(a/w)
   p->cg.ncell = 1;
   for (int d = 0; d < 3; ++d) {
-    int nc = (int)std::floor(2.0 * box[d] / a);
+    int nc = (int)std::floor(kCellDiv * box[d] / a);
     if (nc < 1) nc = 1;
     if (nc > 1024) nc = 1024;
     p->cg.nc[d] = nc;
@@ -434,7 +434,10 @@ int mls6_plan_info(const mls6_plan_t* plan, int* n_grid, double* h_actual, int* 
 int mls6_set_tuning(mls6_plan_t* plan, int split, int groups) {
   if (!plan) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8) return MLS6_ERR_ARG;
+  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8 && split != 16 &&
+      split != 32)
+    return MLS6_ERR_ARG;
+  if (split > 8 && !pair_cluster_ok(p)) return MLS6_ERR_ARG;
   if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return MLS6_ERR_ARG;
   const int s2 = split ? split : p->pair_split;
   const int g2 = (groups && !p->stencil_global) ? groups : p->stencil_groups;

@@ -126,6 +126,56 @@ def test_small_cases_fp64(gpu_lib, orc, name, N, box, a, h, l):
     compare(g, o, TOL64, name)
 
 
+SHAPE_CASES = [c for c in CASES if c[0] in ("two_atoms", "ragged_aniso", "box_below_2a",
+                                            "slab_5_levels", "many_tiles")]
+
+
+# FP32 only where the energy is not a small difference of large terms (with
+# two atoms the self term and the grid part cancel to ~1e-5 of FP32 rounding)
+SHAPE_PARAMS = [c + ("fp64",) for c in SHAPE_CASES] + [
+    c + ("fp32",) for c in SHAPE_CASES if c[1] >= 900]
+
+
+@pytest.mark.parametrize("name,N,box,a,h,l,prec", SHAPE_PARAMS,
+                         ids=[f"{c[0]}-{c[-1]}" for c in SHAPE_PARAMS])
+def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
+    """Every pair-kernel shape (lanes per atom 1..8: one atom per lane
+    group; 16, 32: warp form) against the oracle; the warp form is refused
+    where the neighbour range is too wide for it."""
+    import torch
+
+    region = None
+    if name.startswith("slab"):
+        region = ((0, box[0]), (0, box[1]), (0.35 * box[2], 0.65 * box[2]))
+    x, c = I.uniform_atoms(zlib.crc32(name.encode()) % 10000, N, box, region=region)
+    x, c = as_prec(x, c, prec)
+    n = orc.grid_dims(box, h, l)
+    o = orc.evaluate(box, a, n, l, x, c)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = gpu_lib.Plan(box, N, a, h, l, precision=prec)
+    pos = torch.tensor(np.c_[x, c], dtype=dt, device="cuda")
+    tol = TOL64 if prec == "fp64" else TOL32
+    ran = []
+    for split in (1, 2, 4, 8, 16, 32):
+        try:
+            gpu_lib.mls6_set_tuning(plan.handle, split, 0)
+        except gpu_lib.MLS6Error:
+            assert split > 8, split
+            continue
+        r = plan.evaluate(pos, virial=True, atom_energy=False)
+        torch.cuda.synchronize()
+        out = r["out"].cpu().numpy()
+        g = dict(E=out[0], W=out[1:7], F=r["F"].cpu().double().numpy())
+        compare(g, o, tol, f"{name} split={split}")
+        r2 = plan.evaluate(pos, virial=True, atom_energy=False)
+        torch.cuda.synchronize()
+        assert torch.equal(r["F"], r2["F"]) and torch.equal(r["out"], r2["out"])
+        ran.append(split)
+    assert ran[:4] == [1, 2, 4, 8]
+    if name in ("slab_5_levels", "many_tiles"):
+        assert ran[4:] == [16, 32]
+
+
 def test_no_atoms(gpu_lib):
     g = gpu_eval(gpu_lib, (8.0, 8.0, 8.0), 2.0, 1.0, 3, np.zeros((0, 3)), np.zeros(0), "fp64")
     assert g["E"] == 0.0
