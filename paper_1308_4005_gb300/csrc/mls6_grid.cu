@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
   using U = typename Fixed<T>::U;
   constexpr int kCap = kAnterpBoxBytes / (int)sizeof(U);
   __shared__ U box[kCap];
-  __shared__ int lo[3], hi[3];
+  __shared__ int lo[3], hi[3], sexp;
   const long z = pdl_begin();
   sp += z;
   flag += z;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
     lo[threadIdx.x] = INT_MAX;
     hi[threadIdx.x] = INT_MIN;
   }
-  const T scale = Fixed<T>::pow2(fixed_exponent<T>(flag, span, lbm, lbc));
+  if (threadIdx.x == 0) sexp = fixed_exponent<T>(flag, span, lbm, lbc);
   Vec4<T> p = valid ? sp[i] : Vec4<T>{T(0), T(0), T(0), T(0)};
   if (valid && lbm >= 0) {  // Lorentz-Berthelot channel: xi_m = lbc sigma^m sqrt(2 eps)
     T s = T(1);
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
     atomicMax(&hi[2], b2 + 2);
   }
   __syncthreads();
+  const T scale = Fixed<T>::pow2(sexp);
   const int e0 = hi[0] - lo[0] + 1, e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
   const long vol = (long)e0 * e1 * e2;
   const bool in_box = hi[0] >= lo[0] && vol <= kCap;  // the same for the whole block
@@ -163,15 +164,21 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
         }
     }
   }
-  if (in_box) {
+  if (in_box) {  // flush: one warp per box row (y, z), lanes along x
     __syncthreads();
-    for (int t = threadIdx.x; t < (int)vol; t += blockDim.x) {
-      const U v = box[t];
-      if (v == 0) continue;
-      const int x = t % e0, y = (t / e0) % e1, zz = t / (e0 * e1);
-      const long node = wrapi(lo[0] + x, n0) +
-                        (long)n0 * (wrapi(lo[1] + y, n1) + (long)n1 * wrapi(lo[2] + zz, n2));
-      atomicAdd(&qfx[node], v);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < e1 * e2; r += nw) {
+      const int y = wrapi(lo[1] + r % e1, n1), zz = wrapi(lo[2] + r / e1, n2);
+      const long row = (long)n0 * (y + (long)n1 * zz);
+      const U* br = box + (size_t)r * e0;
+      for (int x = lane; x < e0; x += 32) {
+        const U v = br[x];
+        if (v == 0) continue;
+        int ix = lo[0] + x;  // within a few nodes of [0, n0)
+        while (ix < 0) ix += n0;
+        while (ix >= n0) ix -= n0;
+        atomicAdd(&qfx[row + ix], v);
+      }
     }
   }
 }
@@ -181,12 +188,14 @@ template <typename T>
 __global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
                              const int* __restrict__ flag, double span, T* __restrict__ q,
                              int lbm, double lbc) {
+  __shared__ int sexp;
   const long z = pdl_begin();
   qfx += z; flag += z;
+  if (threadIdx.x == 0) sexp = fixed_exponent<T>(flag, span, lbm, lbc);
+  __syncthreads();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  const T iscale = Fixed<T>::pow2(-fixed_exponent<T>(flag, span, lbm, lbc));
-  q[i] = Fixed<T>::from_fixed((typename Fixed<T>::I)qfx[i], iscale);
+  q[i] = Fixed<T>::from_fixed((typename Fixed<T>::I)qfx[i], Fixed<T>::pow2(-sexp));
 }
 
 // Cells (with periodic images) that a box of width 4h can meet, product
