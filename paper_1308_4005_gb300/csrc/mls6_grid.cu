@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   __shared__ double sh[32 * 7];
   __shared__ bool last;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double ea = 0.0;
+  T ea = T(0);
   if (i < N) {
     Vec4<T> p = sp[i];
     T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
@@ -735,13 +735,15 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     forces[3 * (size_t)o + 0] = floc[3 * (size_t)i + 0] + ci * g0 * ih0;
     forces[3 * (size_t)o + 1] = floc[3 * (size_t)i + 1] + ci * g1 * ih1;
     forces[3 * (size_t)o + 2] = floc[3 * (size_t)i + 2] + ci * g2 * ih2;
-    double cd = (double)ci;
-    ea = -0.5 * cd * ((double)e0[i] + (double)acc) + 0.5 * cself * cd * cd;
-    if (atom_energy) atom_energy[o] = ea;
+    ea = T(-0.5) * ci * (e0[i] + acc) + T(0.5 * cself) * ci * ci;
+    if (atom_energy) atom_energy[o] = (double)ea;
   }
-  double s = block_sum(ea, sh);
+  // block sum in the kernel's precision, promoted per warp (FP64 is slow)
+  T ev[1] = {ea};
+  double s[1];
+  block_sum_lo<T, 1>(ev, s, sh);
   if (threadIdx.x == 0) {
-    epart[blockIdx.x] = s;
+    epart[blockIdx.x] = s[0];
     __threadfence();
     last = atomicAdd(R.ticket, 1u) == gridDim.x - 1;
   }

@@ -256,7 +256,9 @@ def test_slab65536_fp64_sampled(gpu_lib, orc):
 def test_cube1m_fp32_sampled(gpu_lib, orc):
     """N=1,048,576 cube at rho=0.85, a=3, h=1 (112^3), 5 levels, FP32: sampled
     atoms against the oracle (forces and per-atom energies), the total as the
-    double sum of per-atom energies."""
+    sum of per-atom energies (both formed from the same FP32 per-atom values;
+    the total adds them in FP32 within warps, relative rounding of order
+    2^-24 sqrt(32 / (N/32)) ~ 2e-9)."""
     w = I.workload("cube1m")
     x, c = I.generate(w)
     x, c = as_prec(x, c, "fp32")
@@ -267,7 +269,7 @@ def test_cube1m_fp32_sampled(gpu_lib, orc):
     rms = np.sqrt(np.mean(np.sum(g["F"] ** 2, axis=1)))
     assert np.abs(g["F"][idx] - o["F"]).max() <= TOL32["F"] * rms
     assert np.abs(g["eatom"][idx] - o["eatom"]).max() <= TOL32["eatom"] * np.abs(o["eatom"]).max()
-    assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-12)
+    assert g["eatom"].sum() == pytest.approx(g["E"], rel=1e-8)
 
 
 # ------------------------------------------------------ execution modes
