@@ -2,6 +2,8 @@
 // wrap positions into the box, histogram them over cells of width >= a/2,
 // exclusive scan of the counts, scatter into cell order, and order each
 // cell by input index so that every later sum runs in a reproducible order.
+#include <climits>
+
 #include "mls6_device.cuh"
 
 namespace mls6 {
@@ -100,14 +102,31 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int t = 0; t < (int)gridDim.x; ++t) {
-      int v = ((volatile int*)tsum)[t];
-      tsum[t] = acc;
-      acc += v;
+  // exclusive scan of the tile sums, blockDim.x tiles at a time with a
+  // running carry (all loads of a chunk in flight together)
+  int carry = 0;
+  for (int t0 = 0; t0 < (int)gridDim.x; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    const int v = t < (int)gridDim.x ? ((volatile int*)tsum)[t] : 0;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
     }
-    start[n] = acc;
+    __syncthreads();  // shm free (previous chunk / maxima above)
+    if (lane == 31) shm[wid] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int ws = shm[w];
+      if (w < wid) wbase += ws;
+      total += ws;
+    }
+    if (t < (int)gridDim.x) tsum[t] = carry + wbase + incl - v;
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    start[n] = carry;
     *ticket = 0u;
   }
   int mp = 0;
@@ -192,10 +211,14 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
   sidx[slot] = i;
 }
 
-// Insertion sort of each cell by input index (cells above 256 atoms are
-// left in scatter order: results stay correct, only bitwise
-// reproducibility is lost for them).  Also returns the cell's counter to
-// zero for the next binning.
+// Each cell's records sorted by input index, so that every later sum runs
+// in an order that does not depend on the scatter's atomics.  Cells of up
+// to 8 atoms (nearly all at liquid densities with cells of width a/2) are
+// loaded into registers together and sorted by an odd-even transposition
+// network; larger cells use an insertion sort in global memory; cells
+// above 256 atoms are left in scatter order (results stay correct, only
+// bitwise reproducibility is lost for them).  Also returns the cell's
+// counter to zero for the next binning.
 template <typename T>
 __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
                            int* __restrict__ sidx, int* __restrict__ count) {
@@ -204,8 +227,40 @@ __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* _
   long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncell) return;
   count[cell] = 0;
-  int b = start[cell], e = start[cell + 1];
-  if (e - b < 2 || e - b > 256) return;
+  const int b = start[cell], e = start[cell + 1];
+  const int n = e - b;
+  if (n < 2 || n > 256) return;
+  if (n <= 8) {
+    int key[8];
+    Vec4<T> v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      key[k] = INT_MAX;
+      if (k < n) {
+        key[k] = sidx[b + k];
+        v[k] = sorted[b + k];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int k = r & 1; k + 1 < 8; k += 2)
+        if (key[k] > key[k + 1]) {
+          const int tk = key[k];
+          key[k] = key[k + 1];
+          key[k + 1] = tk;
+          const Vec4<T> tv = v[k];
+          v[k] = v[k + 1];
+          v[k + 1] = tv;
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < n) {
+        sidx[b + k] = key[k];
+        sorted[b + k] = v[k];
+      }
+    return;
+  }
   for (int i = b + 1; i < e; ++i) {
     int key = sidx[i];
     Vec4<T> v = sorted[i];
