@@ -1,5 +1,6 @@
 // Grid part of multilevel summation (Sec. II.B): anterpolation, restriction,
 // evaluation on every level, prolongation and interpolation.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -878,10 +879,15 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
     p->stencil_blocks = cdiv(nodes, kBlock);
     return MLS6_OK;
   }
-  // tap-row groups per tile: the smallest of 1, 2, 4 giving about 24
-  // resident warps per SM on a 152-SM GPU
+  // tap-row groups per tile: the smallest of 1, 2, 4 for which the launch
+  // has about 24 warps per SM of a 152-SM GPU in total, and the tiles that
+  // fit in one SM's 227 KB of shared memory hold at least 24 warps
+  // (1M-atom cube, 51 KB tiles: 4 tiles per SM, two groups -> stencil
+  // 511 -> 434 us)
+  const long tiles_per_sm = std::max(1L, (long)(227 * 1024) / (long)p->stencil_smem);
   p->stencil_groups = 1;
-  while (p->stencil_groups < 4 && p->stencil_blocks * 4 * p->stencil_groups < 152L * 24)
+  while (p->stencil_groups < 4 && (p->stencil_blocks * 4 * p->stencil_groups < 152L * 24 ||
+                                   tiles_per_sm * 4 * p->stencil_groups < 24))
     p->stencil_groups *= 2;
   // the limit is a property of the kernel, shared by every plan in the
   // process: set it to the budget ceiling, not to this plan's tile size
