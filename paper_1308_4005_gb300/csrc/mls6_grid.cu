@@ -316,6 +316,7 @@ template <typename T> struct StencilLevel {
 template <typename T> struct StencilArgs {
   StencilLevel<T> lv[kMaxLevels];
   int nlev, P, S, nrows, ntaps;
+  int Sx, Sp;           // padded row and plane pitch of the staged tile
   const int4* rows;     // dy, dz, R, first tap
   const Vec4<T>* wv;    // g_1, G, G dx, G dx^2 per tap
   double hc[6];         // h_x^2, h_y^2, h_z^2, h_x h_y, h_x h_z, h_y h_z (level 1)
@@ -330,6 +331,16 @@ template <typename T> struct StencilArgs {
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Pitches of the staged S^3 tile: a warp reads 8 y-rows x 4 z-planes at one
+// x offset, so an odd row pitch and a plane pitch of 8 mod 16 put its 32
+// lanes in 32 different shared-memory banks (for 8-byte values, 16 lanes
+// per half-warp in 16 bank pairs).
+inline void stencil_pitches(int S, int& Sx, int& Sp) {
+  Sx = S | 1;
+  Sp = S * Sx;
+  while (Sp % 16 != 8) ++Sp;
+}
 
 // Eq. (evaluation) on all levels k < l in one launch.  Block = one 8x8x8
 // output tile of one level; the tile plus a halo of P nodes (periodic) is
@@ -355,9 +366,9 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
       coarsest_node<T, VIR>(A.qt, A.nt[0], A.nt[1], A.nt[2], A.tT, A.tV, A.et, A.wtop, mu);
     return;
   }
-  const int S = A.S, P = A.P, S2 = S * S, S3 = S2 * S;
+  const int S = A.S, P = A.P, S2 = S * S, S3 = S2 * S, Sx = A.Sx, Sp = A.Sp;
   T* tile = reinterpret_cast<T*>(smem_raw);
-  Vec4<T>* wv = reinterpret_cast<Vec4<T>*>(smem_raw + align16(sizeof(T) * S3));
+  Vec4<T>* wv = reinterpret_cast<Vec4<T>*>(smem_raw + align16(sizeof(T) * S * Sp));
   int4* rows = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(wv) +
                                        sizeof(Vec4<T>) * A.ntaps);
   const long b = blockIdx.x;
@@ -376,24 +387,25 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
   for (int i = threadIdx.x; i < S3; i += blockDim.x) {
     int ix = i % S, iy = (i / S) % S, iz = i / S2;
     int gx = wrapi(ox + ix - P, n0), gy = wrapi(oy + iy - P, n1), gz = wrapi(oz + iz - P, n2);
-    tile[i] = q[gx + (long)n0 * (gy + (long)n1 * gz)];
+    tile[iz * Sp + iy * Sx + ix] = q[gx + (long)n0 * (gy + (long)n1 * gz)];
   }
   __syncthreads();
 
   const int lt = threadIdx.x % kStencilThreads, grp = threadIdx.x / kStencilThreads;
-  const int lx = (lt & 1) * kStencilW, ly = (lt >> 1) & 7, lz = lt >> 4;
+  // a warp: 8 y-rows x 4 z-planes at one x offset (conflict-free pitches)
+  const int lx = ((lt >> 6) & 1) * kStencilW, ly = lt & 7, lz = (lt >> 3) & 7;
   const bool row_in = (oy + ly < n1) && (oz + lz < n2);
   T qv[kStencilW];
 #pragma unroll
   for (int w = 0; w < kStencilW; ++w)
-    qv[w] = (row_in && ox + lx + w < n0) ? tile[(lz + P) * S2 + (ly + P) * S + lx + P + w] : T(0);
+    qv[w] = (row_in && ox + lx + w < n0) ? tile[(lz + P) * Sp + (ly + P) * Sx + lx + P + w] : T(0);
   T acc[kStencilW];
 #pragma unroll
   for (int w = 0; w < kStencilW; ++w) acc[w] = T(0);
   T vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0;
   for (int r = grp; r < A.nrows; r += G) {
     const int4 ri = rows[r];
-    const T* in = tile + (lz + P + ri.y) * S2 + (ly + P + ri.x) * S + (lx + P - ri.z);
+    const T* in = tile + (lz + P + ri.y) * Sp + (ly + P + ri.x) * Sx + (lx + P - ri.z);
     const Vec4<T>* ww = wv + ri.w;
     const int nd = 2 * ri.z + 1;
     T b0 = in[0], b1 = in[1], b2 = in[2];
@@ -524,6 +536,7 @@ template <typename T> static StencilArgs<T> stencil_args(Plan* p) {
   A.nlev = p->levels - 1;
   A.P = p->P;
   A.S = kStencilTile + 2 * p->P;
+  stencil_pitches(A.S, A.Sx, A.Sp);
   A.nrows = p->nrows;
   A.ntaps = p->ntaps;
   A.rows = reinterpret_cast<const int4*>(p->d_rows);
@@ -870,7 +883,9 @@ int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_
 template <typename T> int prepare_grid_kernels(Plan* p) {
   if (p->levels < 2) return MLS6_OK;
   const int S = kStencilTile + 2 * p->P;
-  p->stencil_smem = align16(sizeof(T) * S * S * S) + sizeof(Vec4<T>) * p->ntaps +
+  int Sx, Sp;
+  stencil_pitches(S, Sx, Sp);
+  p->stencil_smem = align16(sizeof(T) * S * Sp) + sizeof(Vec4<T>) * p->ntaps +
                     sizeof(int4) * p->nrows;
   p->stencil_global = p->stencil_smem > kStencilSmemMax;
   if (p->stencil_global) {
