@@ -2,6 +2,7 @@
 // wrap positions into the box, histogram them over cells of width >= a/2,
 // exclusive scan of the counts, scatter into cell order, and order each
 // cell by input index so that every later sum runs in a reproducible order.
+#include <algorithm>
 #include <climits>
 
 #include "mls6_device.cuh"
@@ -16,16 +17,25 @@ template <typename T> struct BinArgs {
   int nc[3];
 };
 
-// Also writes, for the fixed-point anterpolation, the block's largest |c|
-// (bmax[block]; reduced by the scan's last block).
+// Also keeps, for the fixed-point anterpolation, the largest |c| in
+// flag[4..5] (a double; one atomic maximum per block on its bits, which
+// order like the value for non-negative doubles), and, when tsum is given
+// (at most kScanDirect tiles), adds the block's atoms per scan tile of
+// kScanTile cells to tsum (a shared-memory histogram first, then one
+// integer atomic per touched tile).
 template <typename T>
 __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
                       BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
-                      int* __restrict__ count, int* __restrict__ flag, T* __restrict__ bmax) {
+                      int* __restrict__ count, int* __restrict__ flag, int* __restrict__ tsum,
+                      int ntiles) {
   const long z = pdl_begin();
   pos += z; cc += z;
   __shared__ T wmax[32];
+  __shared__ int hist[kScanDirect];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tsum)
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
   T cabs = T(0);
   if (i < N) {
     const T* p = pos + (size_t)i * stride;
@@ -50,6 +60,7 @@ __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int s
     v.w = c;
     posw[i] = v;
     atomicAdd(&count[cell], 1);
+    if (tsum) atomicAdd(&hist[cell / kScanTile], 1);
     cabs = fabs(c);
   }
   for (int o = 16; o > 0; o >>= 1) cabs = fmax(cabs, __shfl_xor_sync(0xffffffffu, cabs, o));
@@ -58,52 +69,43 @@ __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int s
   if (threadIdx.x == 0) {
     T m = T(0);
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
-    bmax[blockIdx.x] = m;
+    atomicMax(reinterpret_cast<unsigned long long*>(flag + 4),
+              (unsigned long long)__double_as_longlong((double)m));
   }
+  if (tsum)
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+      if (hist[t]) atomicAdd(&tsum[t], hist[t]);
 }
 
-// Phase 1: per-tile sums and maxima of the cell counts; the last block to
-// finish (ticket counter, reset by that block) turns the tile sums into
-// exclusive tile offsets in one thread, writes the grand total to start[n],
-// and reduces the maxima for the anterpolation's fixed-point scale: the
-// largest cell population to flag[3], the largest |c| (from the binning
-// blocks' bmax) to flag[4..5] as a double.
-template <typename T>
+// Tile pass, for more than kScanDirect tiles: per-tile sums of the cell
+// counts; the last block to finish (ticket counter, reset by that block)
+// turns them into exclusive tile offsets (block-wide scan, blockDim.x tiles
+// at a time with a running carry) and writes the grand total to start[n].
 __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
-                             int* __restrict__ tmax, const T* __restrict__ bmax, int nbin,
                              int* __restrict__ start, int* __restrict__ flag) {
   const long z = pdl_begin();
-  count += z; bmax += z;
-  __shared__ double sh[32];
+  count += z;
   __shared__ int shm[32];
-  __shared__ double shc[32];
   __shared__ bool last;
   unsigned* ticket = reinterpret_cast<unsigned*>(flag + 2);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  long base = (long)blockIdx.x * kScanTile;
-  int s = 0, m = 0;
+  const long base = (long)blockIdx.x * kScanTile;
+  int s = 0;
   for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
-    if (base + t < n) {
-      const int v = count[base + t];
-      s += v;
-      m = max(m, v);
-    }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) shm[wid] = m;
-  double tot = block_sum((double)s, sh);  // synchronises: shm complete
+    if (base + t < n) s += count[base + t];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) shm[wid] = s;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int mm = 0;
-    for (int w = 0; w < nw; ++w) mm = max(mm, shm[w]);
-    tsum[blockIdx.x] = (int)tot;
-    tmax[blockIdx.x] = mm;
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += shm[w];
+    tsum[blockIdx.x] = tot;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // exclusive scan of the tile sums, blockDim.x tiles at a time with a
-  // running carry (all loads of a chunk in flight together)
   int carry = 0;
   for (int t0 = 0; t0 < (int)gridDim.x; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
@@ -113,7 +115,7 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
       const int u = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += u;
     }
-    __syncthreads();  // shm free (previous chunk / maxima above)
+    __syncthreads();  // shm free (previous chunk / tile sums above)
     if (lane == 31) shm[wid] = incl;
     __syncthreads();
     int wbase = 0, total = 0;
@@ -129,56 +131,53 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
     start[n] = carry;
     *ticket = 0u;
   }
-  int mp = 0;
-  double mc = 0.0;
-  for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x)
-    mp = max(mp, ((volatile int*)tmax)[t]);
-  for (int t = threadIdx.x; t < nbin; t += blockDim.x) mc = fmax(mc, (double)bmax[t]);
-  for (int o = 16; o > 0; o >>= 1) {
-    mp = max(mp, __shfl_xor_sync(0xffffffffu, mp, o));
-    mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-  }
-  __syncthreads();
-  if (lane == 0) {
-    shm[wid] = mp;
-    shc[wid] = mc;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < nw; ++w) {
-      mp = max(mp, shm[w]);
-      mc = fmax(mc, shc[w]);
-    }
-    flag[3] = mp;
-    *reinterpret_cast<double*>(flag + 4) = mc;
-  }
 }
 
-// Phase 3: scan inside each tile (256 threads x 8 consecutive cells), write
-// start[], reset count[] for use as fill counters by the scatter.
-__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ toff,
-                             int* __restrict__ start) {
+// Scan inside each tile (256 threads x 8 consecutive cells), write start[],
+// reset count[] for use as fill counters by the scatter, and keep the
+// largest cell population in flag[3] (one atomic maximum per block).  The
+// tile's offset is tsum[tile] from the tile pass, or (direct: at most
+// kScanDirect tiles, tsum holding the tile sums from the binning) the sum of
+// the preceding tiles' sums, formed by each block; the last tile then also
+// writes the grand total to start[n].
+__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ tsum,
+                             int* __restrict__ start, int direct, int* __restrict__ flag) {
   const long z = pdl_begin();
-  toff += z;
-  __shared__ int wsum[32];
+  tsum += z;
+  __shared__ int wsum[32], wmx[32];
+  __shared__ int toff;
   constexpr int PER = kScanTile / 256;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * PER;
-  int v[PER], s = 0;
+  int v[PER], s = 0, mx = 0;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     v[k] = (base + k < n) ? count[base + k] : 0;
     s += v[k];
+    mx = max(mx, v[k]);
   }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int pre = 0;  // direct: this thread's share of the preceding tiles' sums
+  if (direct)
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) pre += tsum[t];
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  }
   int incl = s;
   for (int o = 1; o < 32; o <<= 1) {
     int u = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += u;
   }
   if (lane == 31) wsum[wid] = incl;
+  if (lane == 0) wmx[wid] = direct ? pre : 0;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < nw; ++w) acc += wmx[w];
+    toff = direct ? acc : tsum[blockIdx.x];
+  }
   if (wid == 0) {
-    int x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    int x = lane < nw ? wsum[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
       int u = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += u;
@@ -186,7 +185,8 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
     wsum[lane] = x;
   }
   __syncthreads();
-  int excl = incl - s + (wid > 0 ? wsum[wid - 1] : 0) + toff[blockIdx.x];
+  if (lane == 0) wmx[wid] = mx;  // wmx read above by thread 0 before this barrier
+  int excl = incl - s + (wid > 0 ? wsum[wid - 1] : 0) + toff;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     if (base + k < n) {
@@ -194,6 +194,13 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
       count[base + k] = 0;
     }
     excl += v[k];
+  }
+  if (direct && threadIdx.x == blockDim.x - 1 && blockIdx.x == gridDim.x - 1) start[n] = excl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < nw; ++w) m = max(m, wmx[w]);
+    atomicMax(flag + 3, m);
   }
 }
 
@@ -218,13 +225,15 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
 // network; larger cells use an insertion sort in global memory; cells
 // above 256 atoms are left in scatter order (results stay correct, only
 // bitwise reproducibility is lost for them).  Also returns the cell's
-// counter to zero for the next binning.
+// counter, and the first nreset tile sums, to zero for the next binning.
 template <typename T>
 __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
-                           int* __restrict__ sidx, int* __restrict__ count) {
+                           int* __restrict__ sidx, int* __restrict__ count,
+                           int* __restrict__ tsum, int nreset) {
   const long z = pdl_begin();
   start += z;
   long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell < nreset) tsum[cell] = 0;
   if (cell >= ncell) return;
   count[cell] = 0;
   const int b = start[cell], e = start[cell + 1];
@@ -286,20 +295,26 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
   }
   const long ncell = p->cg.ncell;
   const long ntiles = cdiv(ncell, kScanTile);
+  // direct: tile sums from the binning (kept zero between binnings by the
+  // cell sort; zeroed at plan creation), no tile pass
+  const bool direct = ntiles <= kScanDirect;
   // cell counters start at zero: set at plan creation, reset by k_cellsort
   const int nbin = (int)cdiv(N, kBlock);
   launch_pdl(k_bin<T>, nbin, kBlock, 0, st, pos, cc, cc ? 3 : 4, N, bg, (Vec4<T>*)p->d_pos_w,
-                                    p->d_cell_of, p->d_cell_count, p->d_flag, (T*)p->d_bmax);
-  launch_pdl(k_scan_tiles<T>, ntiles, kBlock, 0, st, p->d_cell_count, ncell, p->d_scan, p->d_scan + ntiles,
-                                             (const T*)p->d_bmax, nbin, p->d_cell_start,
-                                             p->d_flag);
-  launch_pdl(k_scan_final, ntiles, kBlock, 0, st, p->d_cell_count, ncell, p->d_scan, p->d_cell_start);
+             p->d_cell_of, p->d_cell_count, p->d_flag, direct ? p->d_scan : (int*)nullptr,
+             (int)ntiles);
+  if (!direct)
+    launch_pdl(k_scan_tiles, ntiles, kBlock, 0, st, (const int*)p->d_cell_count, ncell, p->d_scan,
+               p->d_cell_start, p->d_flag);
+  launch_pdl(k_scan_final, ntiles, kBlock, 0, st, p->d_cell_count, ncell, (const int*)p->d_scan,
+             p->d_cell_start, direct ? 1 : 0, p->d_flag);
   launch_pdl(k_scatter<T>, cdiv(N, kBlock), kBlock, 0, st, (const Vec4<T>*)p->d_pos_w, p->d_cell_of, N,
                                                   p->d_cell_start, p->d_cell_count,
                                                   (Vec4<T>*)p->d_sorted, p->d_sorted_idx);
-  launch_pdl(k_cellsort<T>, cdiv(ncell, kBlock), kBlock, 0, st, 
-      p->d_cell_start, ncell, (Vec4<T>*)p->d_sorted, p->d_sorted_idx, p->d_cell_count);
-  return 5;
+  launch_pdl(k_cellsort<T>, cdiv(std::max(ncell, ntiles), kBlock), kBlock, 0, st,
+             (const int*)p->d_cell_start, ncell, (Vec4<T>*)p->d_sorted, p->d_sorted_idx,
+             p->d_cell_count, p->d_scan, direct ? (int)ntiles : 0);
+  return direct ? 4 : 5;
 }
 
 template int launch_bin<float>(Plan*, const float*, const float*, cudaStream_t);

@@ -65,7 +65,6 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_cell_count, sizeof(int) * p->cg.ncell);
   rc |= A((void**)&p->d_cell_start, sizeof(int) * (p->cg.ncell + 1));
   rc |= A((void**)&p->d_scan, 2 * sizeof(int) * std::max(1L, cdiv(p->cg.ncell, kScanTile)));
-  rc |= A(&p->d_bmax, sizeof(T) * std::max(1L, cdiv(N, kBlock)));
   rc |= A(&p->d_sorted, sizeof(Vec4<T>) * N);
   rc |= A((void**)&p->d_sorted_idx, sizeof(int) * N);
   rc |= A(&p->d_e0, e * N);
@@ -146,6 +145,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
                 cudaMemcpyHostToDevice));
   CK(cudaMemset(p->d_flag, 0, sizeof(int) * 8));
   CK(cudaMemset(p->d_cell_count, 0, sizeof(int) * p->cg.ncell));  // reset by each binning
+  CK(cudaMemset(p->d_scan, 0, 2 * sizeof(int) * std::max(1L, cdiv(p->cg.ncell, kScanTile))));
   CK(cudaMemset(p->d_wpart, 0, 6 * sizeof(double) * p->n_wpart));
   return MLS6_OK;
 }

@@ -15,6 +15,12 @@ namespace mls6 {
 constexpr int kMaxLevels = 12;
 constexpr int kBlock = 256;
 constexpr int kScanTile = 2048;   // cells per block in the cell-count scan
+// Up to this many scan tiles the binning blocks add their atoms per tile
+// (one global atomic per touched tile and block) and the tile pass is
+// skipped; beyond it the per-block atomics cost more than the pass
+// (65,536-atom slab, 27 tiles: bin stage 23.4 -> 18.0 us; 1M cube, 175 tiles:
+// 69 -> 80 us).
+constexpr int kScanDirect = 64;
 constexpr int kStencilTile = 8;   // output tile edge of the level-stencil kernel
 constexpr int kStencilThreads = 128;
 constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
@@ -90,7 +96,6 @@ struct Plan {
   void* d_e0 = nullptr;        // T[N] local potential (sorted order)
   void* d_floc = nullptr;      // T[3N] local forces (sorted order)
   void* d_q1fx = nullptr;      // int32 (FP32 modes) / int64 (FP64) fixed-point anterpolation sums
-  void* d_bmax = nullptr;      // T[N/256]: largest |c| per binning block
   void* d_lbw = nullptr;       // T[N]: sqrt(2 eps) in sorted order (Lorentz-Berthelot)
   void* d_lbpot = nullptr;     // T[7 n_1]: level-1 total potential of each LB channel
   void* d_q[kMaxLevels + 1] = {};
@@ -108,7 +113,7 @@ struct Plan {
   // current split are written and summed)
   long wpart_stencil = 0, wpart_top = 0, wpart_pair = 0;
   double* d_out = nullptr;     // [0] energy, [1..6] virial
-  int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] scan ticket,
+  int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] tile-pass ticket,
                                // [3] max cell population, [4..5] max |c| (double),
                                // [6..7] max sqrt(2 eps) (double, Lorentz-Berthelot)
   double* h_out = nullptr;     // pinned host staging of d_out

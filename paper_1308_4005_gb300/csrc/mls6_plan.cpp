@@ -237,7 +237,7 @@ static void free_plan(Plan* p) {
   void* ptrs[] = {p->d_pos_w, p->d_cell_of, p->d_cell_count, p->d_cell_start, p->d_sorted,
                   p->d_sorted_idx, p->d_e0, p->d_floc, p->d_rows, p->d_wv, p->d_top_T,
                   p->d_top_V, p->d_epart, p->d_wpart, p->d_out, p->d_flag, p->d_scan,
-                  p->d_q1fx, p->d_tcw, p->d_bmax, p->d_lbw, p->d_lbpot};
+                  p->d_q1fx, p->d_tcw, p->d_lbw, p->d_lbpot};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 1; k <= kMaxLevels; ++k) {
