@@ -116,7 +116,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   p->n_wpart = p->wpart_pair + p->n_pair_blocks;
   rc |= A((void**)&p->d_epart, sizeof(double) * p->n_epart);
   rc |= A((void**)&p->d_wpart, 6 * sizeof(double) * p->n_wpart);
-  rc |= A((void**)&p->d_out, 8 * sizeof(double));
+  rc |= A((void**)&p->d_out, (8 + 6 * kReduceGroups) * sizeof(double));
   rc |= A((void**)&p->d_flag, sizeof(int) * 8);
   rc |= A(&p->d_q1fx, sizeof(unsigned long long) * p->lv[1].np);
   if (rc) return MLS6_ERR_NOMEM;

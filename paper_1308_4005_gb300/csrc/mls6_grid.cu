@@ -697,6 +697,8 @@ struct ReduceArgs {
   int vir;
   double* out;
   unsigned* ticket;
+  double* gsum;  // ng slice sums of the virial records (6 doubles each)
+  int ng;
 };
 
 template <typename T>
@@ -756,6 +758,23 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   T ev[1] = {ea};
   double s[1];
   block_sum_lo<T, 1>(ev, s, sh);
+  // With several waves of blocks, warp 0 of each of the first ng blocks sums
+  // one contiguous slice of the virial records (fixed order) and the last
+  // block adds the ng slice sums instead of every record (one block summing
+  // ~7,600 records in FP64 took 22 us on a 1M-atom cube).  In a single wave
+  // the slices would lengthen the kernel instead, and ng is 0.
+  if (R.vir && (int)blockIdx.x < R.ng && threadIdx.x < 32) {
+    const long per = (R.nw + R.ng - 1) / R.ng, k0 = (long)blockIdx.x * per;
+    const long k1 = min(R.nw, k0 + per);
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long k = k0 + threadIdx.x; k < k1; k += 32)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[c] += R.wpart[6 * k + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) R.gsum[6 * blockIdx.x + c] = v[c];
+  }
   if (threadIdx.x == 0) {
     epart[blockIdx.x] = s[0];
     __threadfence();
@@ -764,7 +783,10 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   __syncthreads();
   if (last) {
     __threadfence();
-    final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
+    if (R.ng > 0)
+      final_reduce(epart, gridDim.x, R.gsum, R.ng, R.vir, R.out, sh);
+    else
+      final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
     if (threadIdx.x == 0) *R.ticket = 0u;
   }
 }
@@ -868,7 +890,8 @@ int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
   ReduceArgs R = {p->d_wpart, wpart_used(p), vir ? 1 : 0, p->d_out,
-                  reinterpret_cast<unsigned*>(p->d_flag + 1)};
+                  reinterpret_cast<unsigned*>(p->d_flag + 1), p->d_out + 8,
+                  cdiv(N, kBlock) >= 4L * 152 ? kReduceGroups : 0};
   launch_pdl(k_interp<T>, cdiv(N, kBlock), kBlock, 0, st, 
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
       L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,

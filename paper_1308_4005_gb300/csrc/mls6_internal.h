@@ -15,6 +15,7 @@ namespace mls6 {
 constexpr int kMaxLevels = 12;
 constexpr int kBlock = 256;
 constexpr int kScanTile = 2048;   // cells per block in the cell-count scan
+constexpr int kReduceGroups = 64; // interpolation blocks that pre-reduce slices of the virial records
 // Up to this many scan tiles the binning blocks add their atoms per tile
 // (one global atomic per touched tile and block) and the tile pass is
 // skipped; beyond it the per-block atomics cost more than the pass
@@ -112,7 +113,7 @@ struct Plan {
   // pair blocks (room for the largest lane split; only the records of the
   // current split are written and summed)
   long wpart_stencil = 0, wpart_top = 0, wpart_pair = 0;
-  double* d_out = nullptr;     // [0] energy, [1..6] virial
+  double* d_out = nullptr;     // [0] energy, [1..6] virial; [8..] kReduceGroups slice sums of 6
   int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] tile-pass ticket,
                                // [3] max cell population, [4..5] max |c| (double),
                                // [6..7] max sqrt(2 eps) (double, Lorentz-Berthelot)
