@@ -701,7 +701,7 @@ struct ReduceArgs {
   int ng;
 };
 
-template <typename T>
+template <typename T, bool SLICES>
 __global__ void __launch_bounds__(kBlock) k_interp(
     const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ et,
     int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   // block adds the ng slice sums instead of every record (one block summing
   // ~7,600 records in FP64 took 22 us on a 1M-atom cube).  In a single wave
   // the slices would lengthen the kernel instead, and ng is 0.
-  if (R.vir && (int)blockIdx.x < R.ng && threadIdx.x < 32) {
+  if (SLICES && R.vir && (int)blockIdx.x < R.ng && threadIdx.x < 32) {
     const long per = (R.nw + R.ng - 1) / R.ng, k0 = (long)blockIdx.x * per;
     const long k1 = min(R.nw, k0 + per);
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   __syncthreads();
   if (last) {
     __threadfence();
-    if (R.ng > 0)
+    if (SLICES)
       final_reduce(epart, gridDim.x, R.gsum, R.ng, R.vir, R.out, sh);
     else
       final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
@@ -889,10 +889,14 @@ template <typename T>
 int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
+  // slice sums only for interpolations of several waves: the single-wave
+  // instantiation keeps the smaller kernel (one final-reduction copy)
+  const bool slices = cdiv(N, kBlock) >= 4L * 152;
   ReduceArgs R = {p->d_wpart, wpart_used(p), vir ? 1 : 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1), p->d_out + 8,
-                  cdiv(N, kBlock) >= 4L * 152 ? kReduceGroups : 0};
-  launch_pdl(k_interp<T>, cdiv(N, kBlock), kBlock, 0, st, 
+                  slices ? kReduceGroups : 0};
+  auto kern = slices ? k_interp<T, true> : k_interp<T, false>;
+  launch_pdl(kern, cdiv(N, kBlock), kBlock, 0, st,
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
       L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,
       (const T*)p->d_floc, p->c_self, forces, atom_energy, p->d_epart, R);
