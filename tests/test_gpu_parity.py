@@ -176,6 +176,41 @@ def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
         assert ran[4:] == [16, 32]
 
 
+def test_virial_strain_derivative_many_blocks(gpu_lib):
+    """W_aa = -dE/d eps_aa (reading R8: the grids deform with the box) on a
+    system large enough that the interpolation runs in several waves and its
+    first blocks sum the virial records in slices (>= 608 blocks of 256
+    atoms): the library's FP64 virial against central differences of its own
+    energy under a diagonal strain (the grid counts stay fixed)."""
+    import torch
+
+    L = 57.0
+    N = int(0.85 * L ** 3)
+    assert (N + 255) // 256 >= 608
+    box, a, h, l = (L, L, L), 2.5, 1.0, 4
+    x, c = I.uniform_atoms(4242, N, box)
+
+    def energy_virial(scale):
+        b = tuple(L * s for s in scale)
+        plan = gpu_lib.Plan(b, N, a, h, l, precision="fp64")
+        pos = torch.tensor(np.c_[x * np.array(scale), c], dtype=torch.float64, device="cuda")
+        r = plan.evaluate(pos, virial=True, atom_energy=False)
+        torch.cuda.synchronize()
+        out = r["out"].cpu().numpy().copy()
+        plan.close()
+        return out[0], out[1:7]
+
+    _, W = energy_virial((1.0, 1.0, 1.0))
+    d = 1e-5
+    for k in range(3):
+        sp = [1.0, 1.0, 1.0]
+        sm = [1.0, 1.0, 1.0]
+        sp[k] += d
+        sm[k] -= d
+        fd = -(energy_virial(sp)[0] - energy_virial(sm)[0]) / (2 * d)
+        assert W[k] == pytest.approx(fd, rel=2e-5), (k, W[k], fd)
+
+
 def test_no_atoms(gpu_lib):
     g = gpu_eval(gpu_lib, (8.0, 8.0, 8.0), 2.0, 1.0, 3, np.zeros((0, 3)), np.zeros(0), "fp64")
     assert g["E"] == 0.0
