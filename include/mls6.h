@@ -90,7 +90,8 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
  * every table on the host in FP64, and allocates all device workspace (the
  * plan owns it).  box: 3 doubles.  N: number of atoms (>= 0), fixed for the
  * plan.  a: local cutoff (> 0).  h: requested finest spacing (> 0).
- * levels: number of grid levels l (1..12).  order: interpolation order, 3.
+ * levels: number of grid levels l (1..12), or 0 for the automatic rule of
+ * mls6_auto_levels.  order: interpolation order, 3.
  * precision: mls6_precision.  *out receives the plan (NULL on error). */
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision);
