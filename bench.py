@@ -46,7 +46,8 @@ FLOP_TAP_VIR = 12       # ... plus six virial multiply-adds
 # its capture has no entry and reports null.
 TRAFFIC = {("slab65536", "fp32", "pair"): 1.190144e6,
            ("cube1m", "fp32", "stencil"): 6.509568e6,
-           ("cube1m", "fp32", "pair"): None}
+           ("cube1m", "fp32", "pair"): 1.8241792e7,
+           ("cube1m", "mixed", "pair"): 1.8241792e7}
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}
