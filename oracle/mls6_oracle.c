@@ -9,8 +9,7 @@
  * parallel loop writes only its own output slot and every sum over slots is
  * a serial loop, so results do not depend on the thread count.
  *
- * Readings of the paper that this file takes (each also listed in the
- * design notes of the repository):
+ * Readings of the paper that this file takes:
  *  R1 basis scale: phi^k uses the level-k spacing 2^(k-1) h (Eq. def-phi
  *     prints 2^k h; Sec. III.D gives grid k the spacing 2^(k-1) h).
  *  R2 Eq. (evaluation) applies g_k of Eqs. (g_0), (g_k), (g_l); on levels
@@ -268,6 +267,14 @@ typedef struct {
   double* s;         /* wrapped fractional positions, N*3 */
   double* x;         /* wrapped Cartesian positions, N*3 */
   const double* c;
+  /* linked cells of the local part (Sec. III.D): nc[d] cells per axis of
+   * fractional width 1/nc[d] >= the cutoff's fractional half-extent, so the
+   * neighbours of an atom lie in the K[d] unwrapped cells either side;
+   * atoms of cell m are cell_atoms[cell_start[m] .. cell_start[m+1]-1] in
+   * increasing index */
+  long nc[3], K[3];
+  int64_t* cell_start;
+  int64_t* cell_atoms;
   double* q[21];     /* xi^k (Eq. anterpolation / restriction) */
   double* e[21];     /* e^k (Eq. evaluation) */
   double* et[21];    /* e^{k,tot} (prolongation) */
@@ -277,6 +284,8 @@ typedef struct {
 static void ctx_free(ctx_t* C) {
   free(C->s);
   free(C->x);
+  free(C->cell_start);
+  free(C->cell_atoms);
   for (int k = 1; k <= C->l; ++k) {
     free(C->q[k]);
     free(C->e[k]);
@@ -324,6 +333,37 @@ static int ctx_init(ctx_t* C, const double H[9], double a, const int n[3], int l
     }
     mv3(C->H, si, C->x + 3 * i);
   }
+  /* Cell list: fractional cutoff extent A[d] = a |row d of H^-1|. */
+  long ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    double A = a * rownorm(C->G, d);
+    double m = floor(1.0 / A);
+    if (m > 1024.0) m = 1024.0;
+    C->nc[d] = m < 1.0 ? 1 : (long)m;
+    C->K[d] = (long)ceil(A * (double)C->nc[d]);
+    ncell *= C->nc[d];
+  }
+  C->cell_start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+  C->cell_atoms = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  long* cell_of = (long*)malloc(sizeof(long) * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) {
+    long m = 0;
+    for (int d = 2; d >= 0; --d) {
+      long u = (long)floor(C->s[3 * i + d] * (double)C->nc[d]);
+      if (u > C->nc[d] - 1) u = C->nc[d] - 1;
+      m = m * C->nc[d] + u;
+    }
+    cell_of[i] = m;
+    C->cell_start[m + 1] += 1;
+  }
+  for (long m = 0; m < ncell; ++m) C->cell_start[m + 1] += C->cell_start[m];
+  {
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    for (long m = 0; m < ncell; ++m) fill[m] = C->cell_start[m];
+    for (int64_t i = 0; i < N; ++i) C->cell_atoms[fill[cell_of[i]]++] = i;
+    free(fill);
+  }
+  free(cell_of);
   return 0;
 }
 
@@ -331,7 +371,58 @@ static int ctx_init(ctx_t* C, const double H[9], double a, const int n[3], int l
 /* Local part, Eq. (g_0): every image pair with r < a.                 */
 /* ------------------------------------------------------------------ */
 
+/* One pair term of Eq. (g_0) for d = x_j - x_i + H n (|d| = r < a). */
+static void local_pair(const ctx_t* C, double ci, double cj, const double d3[3], double r,
+                       double* e0, double F[3], double W[6]) {
+  *e0 += cj * orc_gk(0, C->l, C->a, r);
+  double gp = orc_dgk(0, C->l, C->a, r) / r;
+  for (int d = 0; d < 3; ++d) F[d] -= ci * cj * gp * d3[d];
+  add_outer(W, 0.5 * ci * cj * gp, d3);
+}
+
+/* Linked-cell form (Sec. III.D): candidates are the atoms of the unwrapped
+ * cells u within K cells of atom i's cell on every axis; cell u holds the
+ * periodic image n = floor(u / nc) of the atoms of cell u mod nc, so every
+ * (j, n) with |s_j + n - s_i| within the cutoff's extent is visited exactly
+ * once.  Same terms as the all-pairs loop below, summed in another order. */
 static void local_atom(const ctx_t* C, int64_t i, double* e0, double F[3], double W[6]) {
+  *e0 = 0.0;
+  F[0] = F[1] = F[2] = 0.0;
+  for (int d = 0; d < 6; ++d) W[d] = 0.0;
+  const double* si = C->s + 3 * i;
+  double ci = C->c[i];
+  long cell[3];
+  for (int d = 0; d < 3; ++d) {
+    long u = (long)floor(si[d] * (double)C->nc[d]);
+    cell[d] = u > C->nc[d] - 1 ? C->nc[d] - 1 : u;
+  }
+  for (long u2 = cell[2] - C->K[2]; u2 <= cell[2] + C->K[2]; ++u2)
+    for (long u1 = cell[1] - C->K[1]; u1 <= cell[1] + C->K[1]; ++u1)
+      for (long u0 = cell[0] - C->K[0]; u0 <= cell[0] + C->K[0]; ++u0) {
+        long u[3] = {u0, u1, u2}, n[3], m = 0;
+        for (int d = 2; d >= 0; --d) {
+          long w = wrapi(u[d], C->nc[d]);
+          n[d] = (u[d] - w) / C->nc[d];
+          m = m * C->nc[d] + w;
+        }
+        for (int64_t t = C->cell_start[m]; t < C->cell_start[m + 1]; ++t) {
+          int64_t j = C->cell_atoms[t];
+          if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+          const double* sj = C->s + 3 * j;
+          double ds[3] = {sj[0] + n[0] - si[0], sj[1] + n[1] - si[1], sj[2] + n[2] - si[2]};
+          double d3[3];
+          mv3(C->H, ds, d3);
+          double r = sqrt(d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2]);
+          if (!(r < C->a)) continue;
+          local_pair(C, ci, C->c[j], d3, r, e0, F, W);
+        }
+      }
+}
+
+/* All-pairs form: every atom j and every image n whose fractional offset
+ * can lie within the cutoff.  Kept as the check of the linked cells. */
+static void local_atom_allpairs(const ctx_t* C, int64_t i, double* e0, double F[3],
+                                double W[6]) {
   double A[3];
   for (int d = 0; d < 3; ++d) A[d] = C->a * rownorm(C->G, d);
   *e0 = 0.0;
@@ -355,11 +446,7 @@ static void local_atom(const ctx_t* C, int64_t i, double* e0, double F[3], doubl
           mv3(C->H, t, d3); /* d = x_j - x_i + H n */
           double r = sqrt(d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2]);
           if (!(r < C->a)) continue;
-          double cj = C->c[j];
-          *e0 += cj * orc_gk(0, C->l, C->a, r);
-          double gp = orc_dgk(0, C->l, C->a, r) / r;
-          for (int d = 0; d < 3; ++d) F[d] -= ci * cj * gp * d3[d];
-          add_outer(W, 0.5 * ci * cj * gp, d3);
+          local_pair(C, ci, C->c[j], d3, r, e0, F, W);
         }
   }
 }
@@ -703,8 +790,9 @@ int orc_eval_sample(const double H[9], double a, const int n[3], int levels, dou
   return 0;
 }
 
-int orc_local(const double H[9], double a, int64_t N, const double* x, const double* c,
-              int64_t n_idx, const int64_t* idx, double* e0, double* F) {
+static int local_sample(const double H[9], double a, int64_t N, const double* x,
+                        const double* c, int64_t n_idx, const int64_t* idx, double* e0,
+                        double* F, double* W, int allpairs) {
   ctx_t C;
   int n1[3] = {1, 1, 1};
   int rc = ctx_init(&C, H, a, n1, 1, 1.0, N, x, c);
@@ -720,13 +808,34 @@ int orc_local(const double H[9], double a, int64_t N, const double* x, const dou
 #pragma omp parallel for num_threads(NT) schedule(dynamic, 1)
   for (int64_t t = 0; t < n_idx; ++t) {
     double e, f[3], w[6];
-    local_atom(&C, idx[t], &e, f, w);
+    if (allpairs)
+      local_atom_allpairs(&C, idx[t], &e, f, w);
+    else
+      local_atom(&C, idx[t], &e, f, w);
     if (e0) e0[t] = e;
     if (F)
       for (int d = 0; d < 3; ++d) F[3 * t + d] = f[d];
+    if (W)
+      for (int d = 0; d < 6; ++d) W[6 * t + d] = w[d];
   }
   ctx_free(&C);
   return 0;
+}
+
+int orc_local(const double H[9], double a, int64_t N, const double* x, const double* c,
+              int64_t n_idx, const int64_t* idx, double* e0, double* F) {
+  return local_sample(H, a, N, x, c, n_idx, idx, e0, F, NULL, 0);
+}
+
+int orc_local_allpairs(const double H[9], double a, int64_t N, const double* x,
+                       const double* c, int64_t n_idx, const int64_t* idx, double* e0,
+                       double* F, double* W) {
+  return local_sample(H, a, N, x, c, n_idx, idx, e0, F, W, 1);
+}
+
+int orc_local_cells(const double H[9], double a, int64_t N, const double* x, const double* c,
+                    int64_t n_idx, const int64_t* idx, double* e0, double* F, double* W) {
+  return local_sample(H, a, N, x, c, n_idx, idx, e0, F, W, 0);
 }
 
 int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img, int64_t N,

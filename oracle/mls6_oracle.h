@@ -73,6 +73,17 @@ int orc_eval_sample(const double H[9], double a, const int n[3], int levels, dou
 int orc_local(const double H[9], double a, int64_t N, const double* x, const double* c,
               int64_t n_idx, const int64_t* idx, double* e0, double* F);
 
+/* Local part for the listed atoms by the two loop forms, for checking one
+ * against the other: linked cells (the form every other entry point uses)
+ * and all atoms x all images.  e0 (n_idx), F (n_idx*3) and the per-atom
+ * virial records W (n_idx*6, 1/2 c_i c_j g_0'/r d (x) d summed over j) may
+ * be NULL. */
+int orc_local_cells(const double H[9], double a, int64_t N, const double* x, const double* c,
+                    int64_t n_idx, const int64_t* idx, double* e0, double* F, double* W);
+int orc_local_allpairs(const double H[9], double a, int64_t N, const double* x,
+                       const double* c, int64_t n_idx, const int64_t* idx, double* e0,
+                       double* F, double* W);
+
 /* Stage export: writes, level after level, q^k, e^k and e^{k,tot} (each of
  * n_k points) for k = 1..levels into out (3 * sum_k n_k doubles). */
 int orc_grids(const double H[9], double a, const int n[3], int levels, double r_img,

@@ -58,6 +58,10 @@ def lib():
                                       _dp, C.c_int64, _i64p, _dp, _dp, _dp]
         L.orc_local.restype = C.c_int
         L.orc_local.argtypes = [_dp, C.c_double, C.c_int64, _dp, _dp, C.c_int64, _i64p, _dp, _dp]
+        for name in ("orc_local_cells", "orc_local_allpairs"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [_dp, C.c_double, C.c_int64, _dp, _dp, C.c_int64, _i64p,
+                                         _dp, _dp, _dp]
         L.orc_grids.restype = C.c_int
         L.orc_grids.argtypes = [_dp, C.c_double, _ip, C.c_int, C.c_double, C.c_int64, _dp, _dp, _dp]
         L.orc_top_table.restype = C.c_int
@@ -178,6 +182,23 @@ def local(box, a, x, c, idx):
     if rc:
         raise ValueError(f"orc_local failed ({rc})")
     return e0, F
+
+
+def local_forms(box, a, x, c, idx, form):
+    """Local part for the atoms in idx by one loop form ("cells": linked
+    cells, "allpairs": all atoms x all images): (e0, F, W per atom)."""
+    H = _cell(box)
+    x, c = _atoms(x, c)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    e0 = np.zeros(idx.size)
+    F = np.zeros((idx.size, 3))
+    W = np.zeros((idx.size, 6))
+    fn = {"cells": lib().orc_local_cells, "allpairs": lib().orc_local_allpairs}[form]
+    rc = fn(_d(H), float(a), x.shape[0], _d(x), _d(c), idx.size, idx.ctypes.data_as(_i64p),
+            _d(e0), _d(F), _d(W))
+    if rc:
+        raise ValueError(f"orc_local_{form} failed ({rc})")
+    return e0, F, W
 
 
 def grids(box, a, n, levels, x, c, r_img=0.0):

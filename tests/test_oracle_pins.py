@@ -465,3 +465,65 @@ def test_oracle_is_thread_count_independent(orc):
     assert r1["E"] == r2["E"]
     assert np.array_equal(r1["F"], r2["F"])
     assert np.array_equal(r1["W"], r2["W"])
+
+
+# ------------------------------------------------ loop forms and sampled entry points
+
+def _local_cases():
+    tri = np.array([[9.0, 1.5, -0.7], [0.0, 8.5, 1.1], [0.0, 0.0, 10.0]])
+    return [((8.0, 9.0, 10.0), 2.5, 300, 61),   # every axis holds >= 3 cells
+            ((3.0, 9.0, 12.0), 2.5, 200, 62),   # x thinner than 2a: one cell, images -1..1
+            ((2.0, 7.0, 8.0), 2.5, 60, 63),     # x thinner than a: images -2..2
+            (tri, 2.2, 250, 64)]                # triclinic cell
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_local_linked_cells_equal_all_pairs(orc, case):
+    """The linked-cell local loop (Sec. III.D) visits exactly the (j, image)
+    pairs of the plain all-atoms x all-images loop: e0, forces and virial
+    records agree to rounding for every atom, including boxes thinner than
+    the cutoff and a triclinic cell.  A missed or doubled pair changes a
+    value by a whole pair term (>= 1e-4 of the largest here)."""
+    box, a, N, seed = _local_cases()[case]
+    H = np.diag(box) if np.ndim(box) == 1 else np.asarray(box)
+    rng = np.random.default_rng(seed)
+    x = rng.random((N, 3)) @ H.T + rng.normal(0.0, 3.0, (N, 3))  # some atoms outside the cell
+    c = rng.uniform(0.7, 1.2, N)
+    idx = np.arange(N)
+    e1, F1, W1 = orc.local_forms(box, a, x, c, idx, "cells")
+    e2, F2, W2 = orc.local_forms(box, a, x, c, idx, "allpairs")
+    for u, v in ((e1, e2), (F1, F2), (W1, W2)):
+        assert np.abs(u - v).max() <= 1e-13 * np.abs(v).max()
+    assert np.abs(e2).max() > 0.0
+
+
+def _sample_cases():
+    return [((7.0, 8.0, 9.0), 2.0, 0.7, 3, 200, 71),
+            ((6.0, 6.0, 15.0), 2.2, 0.75, 2, 150, 72),   # anisotropic box
+            ((7.5, 7.5, 7.5), 2.0, 0.9, 1, 120, 73)]     # one level: no level stencils
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_eval_sample_equals_eval(orc, case):
+    """orc_eval_sample (the reference of the large sampled GPU tests) gives,
+    at the listed atoms, the forces and per-atom energies of the full
+    evaluation, its grid energy is the sum of the per-level energies
+    -1/2 q^k . e^k of orc_eval, and orc_local's potentials reproduce the
+    full evaluation's local energy -1/2 sum_i c_i e0_i."""
+    box, a, h, l, N, seed = _sample_cases()[case]
+    x, c = I.uniform_atoms(seed, N, box)
+    n = orc.grid_dims(box, h, l)
+    o = orc.evaluate(box, a, n, l, x, c)
+    idx = np.random.default_rng(seed).permutation(N)[: N // 3]
+    idx = np.r_[idx, idx[:5]]  # repeated indices are allowed
+    s = orc.evaluate_sample(box, a, n, l, x, c, idx)
+    assert np.abs(s["F"] - o["F"][idx]).max() <= 1e-14 * np.abs(o["F"]).max()
+    assert np.abs(s["eatom"] - o["eatom"][idx]).max() <= 1e-14 * np.abs(o["eatom"]).max()
+    le = o["level_energy"]
+    assert s["grid_energy"] == pytest.approx(le[2:l + 2].sum(), rel=1e-14, abs=0)
+    # total = local + self + grid levels
+    assert le[0] + le[1] + le[2:l + 2].sum() == pytest.approx(o["E"], rel=1e-13)
+    e0, Fl = orc.local(box, a, x, c, np.arange(N))
+    assert -0.5 * np.sum(c * e0) == pytest.approx(le[0], rel=1e-13)
+    # the local forces alone sum to zero (pair antisymmetry)
+    assert np.abs(Fl.sum(axis=0)).max() <= 1e-12 * np.abs(Fl).max()
