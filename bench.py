@@ -3,13 +3,21 @@
 
 One step = one full ``mls6_eval`` (bin, local pair part, anterpolation,
 restriction, level stencils, coarsest level, prolongation, interpolation,
-energy/virial reduction) of the 65,536-atom liquid/vacuum slab (40x40x51.2
-slab at rho=0.8 in a periodic 40x40x120 box, C6 in [0.8,1.2], a=3, h=1.25,
-4 levels, FP32 with FP64 energy/virial).  Metric: atom-evals/s (atoms whose
-energy contribution and force one evaluation produces, per second).
+energy/virial reduction).  Metric: atom-evals/s (atoms whose energy
+contribution and force one evaluation produces, per second).
+
+Default workload: the 1,048,576-atom fluid cube (rho = 0.85, C6 in
+[0.5, 1.5], a = 3, h = 1 -> 112^3, 5 levels) in mixed precision (FP32 pair
+kernel and transfers, tensor-core level stencils with BF16 hi+lo operands,
+FP64 coarsest level, energy and virial).  The same run also measures the
+plain FP32 form on the same system, the relative force error eps_F of each
+form against exact forces (direct periodic r^-6 sums on sampled atoms), a
+cutoff sweep giving each form's throughput at eps_F = 1e-4, the learned
+correction (coarse grid plus network) and the batched replicas, and a
+roofline entry for every stage.
 
   --impl ours        (default) the CUDA library through its C ABI
-  --impl reference   the FP64 CPU oracle on the host cores (bounded sample)
+  --impl reference   the FP64 CPU oracle on the host cores (full evaluations)
 
 Under torchrun each rank evaluates an independent replica (different seed)
 on its own GPU; value = atoms of all ranks / max-over-ranks time.
@@ -17,6 +25,7 @@ on its own GPU; value = atoms of all ranks / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import math
 import os
@@ -30,45 +39,47 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FP32_LANES_PER_SM = 128
-FP64_LANES_PER_SM = 2   # GB300 FP64 issue rate per SM per clock (FMA lanes)
-SMS = 152
 # Floating-point operations counted per unit of algorithmic work (fixed
-# tallies, see the design notes):
-FLOP_PAIR = 42          # one pair inside the cutoff: energy + force
+# tallies, independent of how a kernel organises the work):
+FLOP_PAIR = 42          # one ordered pair (i, j) inside the cutoff: e0_i and F_i terms
 FLOP_PAIR_VIR = 12      # ... plus the six virial products
 FLOP_TAP = 2            # one stencil tap (multiply-add) per node
 FLOP_TAP_VIR = 12       # ... plus six virial multiply-adds
+TARGET_EPS = 1e-4       # equal-accuracy point of the metric
+EXACT_R = 20.0          # radius of the direct sums behind the exact sampled forces
 
 
-# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
-# it on the named workload and precision (virial on); a kernel changed since
-# its capture has no entry and reports null.
-TRAFFIC = {("slab65536", "fp32", "pair"): 1.190144e6,
-           ("cube1m", "fp32", "stencil"): 6.509568e6,
-           ("cube1m", "fp32", "pair"): 1.8241792e7,
-           ("cube1m", "mixed", "pair"): 1.8241792e7}
+# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu
+# capture on the named workload and precision (virial on); a kernel changed
+# since its capture has no entry and reports null.
+TRAFFIC = {}
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}
+DEFAULT_PREC = {"cube1m": "mixed"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="slab65536")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default="fp32")
+    ap.add_argument("--workload", default="cube1m")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-virial", action="store_true",
                     help="evaluate energy and forces only (no virial arithmetic)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workloads: keep the seeded configuration")
-    ap.add_argument("--dwell", type=float, default=1.5,
+    ap.add_argument("--quick", action="store_true",
+                    help="main line only: no other forms, sweep, learned or batched runs")
+    ap.add_argument("--dwell", type=float, default=1.0,
                     help="seconds of untimed back-to-back evaluations before timing")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = DEFAULT_PREC.get(a.workload, "fp32")
+    return a
 
 
 # ---------------------------------------------------------------- clocks
@@ -201,39 +212,122 @@ def workload_arrays(name, rank, precision):
 
 
 def count_pairs(x, box, a):
-    """Ordered pairs (i, j) with periodic distance < a (the pair kernel's
-    algorithmic work)."""
+    """Ordered pairs (i, j), i != j, with periodic distance < a (the pair
+    kernel's algorithmic work)."""
     import numpy as np
     from scipy.spatial import cKDTree
 
-    xx = np.mod(np.asarray(x, dtype=np.float64), box)
-    p = cKDTree(xx, boxsize=box).query_pairs(a, output_type="ndarray")
-    return 2 * int(p.shape[0])
+    boxv = np.asarray(box, dtype=np.float64)
+    xx = np.mod(np.asarray(x, dtype=np.float64), boxv)
+    t = cKDTree(xx, boxsize=boxv)
+    r = np.nextafter(a, 0.0)  # count_neighbors counts distance <= r
+    return int(t.count_neighbors(t, r)) - xx.shape[0]
+
+
+def exact_forces(x, c, box, idx, R=EXACT_R):
+    """Forces on the atoms idx of the exact periodic r^-6 energy
+    E = -1/2 sum_i sum_{j,n}' c_i c_j |x_j - x_i + nL|^-6, summed directly
+    over every image within R.  The neglected remainder beyond R is the
+    field of the density fluctuations there (a uniform medium exerts no
+    net force): of order 6 c^2 (4 pi rho / (11 R^11))^(1/2) ~ 1e-6 at
+    R = 20 for a fluid, and of order 1.5 pi rho R^-4 ~ 2e-5 near a slab
+    surface, both far below the 1e-4 force errors measured with it."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+
+    L = np.asarray(box, dtype=np.float64)
+    xw = np.mod(np.asarray(x, dtype=np.float64), L)
+    c = np.asarray(c, dtype=np.float64)
+    idx = np.asarray(idx)
+    if np.all(L > 2.0 * R):  # one image at most: periodic tree, minimum image
+        tree, src, pts = cKDTree(xw, boxsize=L), None, xw
+    else:  # replicate the box so every image within R is an explicit point
+        reps = [range(-int(math.ceil(R / l)), int(math.ceil(R / l)) + 1) for l in L]
+        sh = np.array(list(itertools.product(*reps)), dtype=np.float64) * L
+        pts = (xw[None, :, :] + sh[:, None, :]).reshape(-1, 3)
+        src = np.tile(np.arange(xw.shape[0]), sh.shape[0])
+        tree = cKDTree(pts)
+    F = np.zeros((idx.size, 3))
+    for s in range(0, idx.size, 128):
+        ii = idx[s:s + 128]
+        nb = tree.query_ball_point(xw[ii], R, return_sorted=False)
+        cnt = np.array([len(v) for v in nb])
+        jj = np.concatenate([np.asarray(v, dtype=np.int64) for v in nb])
+        owner = np.repeat(np.arange(ii.size), cnt)
+        d = pts[jj] - xw[ii][owner]
+        if src is None:
+            d -= L * np.round(d / L)
+            cj = c[jj]
+        else:
+            cj = c[src[jj]]
+        r2 = np.sum(d * d, axis=1)
+        keep = r2 > 1e-20  # the atom itself
+        w = np.where(keep, 6.0 * cj / np.where(keep, r2, 1.0) ** 4, 0.0)
+        for k in range(3):
+            F[s:s + ii.size, k] = np.bincount(owner, weights=w * d[:, k], minlength=ii.size)
+        F[s:s + ii.size] *= c[ii][:, None]
+    return F
+
+
+def eps_F(F, Fex):
+    import numpy as np
+
+    F = np.asarray(F, dtype=np.float64)
+    return float(np.sqrt(np.sum((F - Fex) ** 2) / np.sum(Fex ** 2)))
+
+
+def at_target(points, target=TARGET_EPS):
+    """Throughput at eps_F = target by log-log interpolation between the
+    bracketing points of a cutoff sweep (extrapolated from the nearest two
+    when the sweep does not bracket it)."""
+    import numpy as np
+
+    pts = sorted([p for p in points if p.get("eps_F")], key=lambda p: p["eps_F"])
+    if len(pts) < 2:
+        return {"value": None, "how": "fewer than two points"}
+    le = np.log([p["eps_F"] for p in pts])
+    lv = np.log([p["value"] for p in pts])
+    t = math.log(target)
+    j = int(np.clip(np.searchsorted(le, t), 1, len(pts) - 1))
+    f = (t - le[j - 1]) / (le[j] - le[j - 1])
+    how = "interpolated" if le[0] <= t <= le[-1] else "extrapolated"
+    return {"value": float(math.exp(lv[j - 1] + f * (lv[j] - lv[j - 1]))), "how": how}
 
 
 # ------------------------------------------------------------ CPU oracle
 
-def _oracle_parts(O, w, xd, cd, S, rng):
-    """Seconds for the oracle's grid part (all atoms) and for its local part
-    over S random atoms."""
+def oracle_full(O, w, xd, cd):
+    """Seconds of one full FP64 oracle evaluation on the current threads."""
+    n = O.grid_dims(w.box, w.h, w.levels)
+    t0 = time.perf_counter()
+    O.evaluate(w.box, w.a, n, w.levels, xd, cd)
+    return time.perf_counter() - t0
+
+
+def oracle_single_thread(O, w, xd, cd, frac=16):
+    """Single-thread oracle time of a full evaluation from a bounded sample:
+    the whole grid part once and the local part of 1/frac of the atoms."""
     import numpy as np
 
     n = O.grid_dims(w.box, w.h, w.levels)
-    t0 = time.perf_counter()
-    O.evaluate_sample(w.box, w.a, n, w.levels, xd, cd, np.zeros(0, np.int64))
-    t_grid = time.perf_counter() - t0
-    idx = rng.choice(w.N, S, replace=False)
-    t0 = time.perf_counter()
-    O.local(w.box, w.a, xd, cd, idx)
-    t_loc = time.perf_counter() - t0
-    return t_grid, t_loc
+    O.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.evaluate_sample(w.box, w.a, n, w.levels, xd, cd, np.zeros(0, np.int64))
+        t_grid = time.perf_counter() - t0
+        idx = np.random.default_rng(7).choice(w.N, max(1, w.N // frac), replace=False)
+        t0 = time.perf_counter()
+        O.local(w.box, w.a, xd, cd, idx)
+        t_loc = (time.perf_counter() - t0) * w.N / idx.size
+    finally:
+        O.set_threads(os.cpu_count() or 1)
+    return t_grid + t_loc, (f"grid part for all {w.N} atoms ({t_grid:.1f} s) + local part for "
+                            f"{idx.size} random atoms, scaled to all ({t_loc:.1f} s)")
 
 
-def oracle_baseline(w, x, c, budget_s=15.0):
-    """Time the FP64 oracle on the host cores on a bounded sample: the whole
-    grid part (anterpolation .. interpolation, all atoms) once, and the local
-    part for a random sample of S atoms; the full-evaluation time is
-    t_grid + t_local(S) * N / S."""
+def oracle_baseline(w, x, c):
+    """The FP64 oracle on the host cores: one full evaluation on all cores
+    (value), and a single-thread figure from a bounded sample."""
     import numpy as np
 
     from oracle import oracle as O
@@ -241,17 +335,11 @@ def oracle_baseline(w, x, c, budget_s=15.0):
     O.build()
     O.set_threads(os.cpu_count() or 1)
     xd, cd = np.asarray(x, np.float64), np.asarray(c, np.float64)
-    rng = np.random.default_rng(7)
-    S = min(w.N, 256)
-    t_grid, t_loc = _oracle_parts(O, w, xd, cd, S, rng)
-    S2 = int(min(w.N, max(S, S * max(budget_s - t_grid, 1.0) / max(t_loc, 1e-6))))
-    t_grid, t_loc2 = _oracle_parts(O, w, xd, cd, S2, rng)
-    t_full = t_grid + t_loc2 * w.N / S2
-    return {"value": w.N / t_full, "unit": "atom-evals/s", "cores": O.threads(),
-            "kind": "oracle",
-            "sample": (f"FP64 oracle, {w.name}: grid part for all {w.N} atoms "
-                       f"({t_grid:.2f} s) + local part for {S2} random atoms ({t_loc2:.2f} s), "
-                       f"full evaluation extrapolated to {t_full:.1f} s")}
+    t_all = oracle_full(O, w, xd, cd)
+    t_one, how = oracle_single_thread(O, w, xd, cd)
+    return {"value": w.N / t_all, "unit": "atom-evals/s", "cores": O.threads(), "kind": "oracle",
+            "sample": f"one full FP64 oracle evaluation of {w.name} on all cores ({t_all:.1f} s)",
+            "single_thread": {"value": w.N / t_one, "cores": 1, "sample": how}}
 
 
 def run_reference(args):
@@ -267,17 +355,12 @@ def run_reference(args):
     O.build()
     O.set_threads(os.cpu_count() or 1)
     xd, cd = np.asarray(x, np.float64), np.asarray(c, np.float64)
-    rng = np.random.default_rng(11)
-    S = min(w.N, max(1, w.N // 32))
     for _ in range(args.warmup):
-        _oracle_parts(O, w, xd, cd, S, rng)
-    full, tg = [], []
-    for _ in range(args.steps):
-        t_grid, t_loc = _oracle_parts(O, w, xd, cd, S, rng)
-        tg.append(t_grid)
-        full.append(t_grid + t_loc * w.N / S)
-    ms = 1e3 * statistics.mean(full)
+        oracle_full(O, w, xd, cd)
+    secs = [oracle_full(O, w, xd, cd) for _ in range(args.steps)]
+    ms = 1e3 * statistics.mean(secs)
     value = w.N / (ms / 1e3)
+    t_one, how = oracle_single_thread(O, w, xd, cd)
     line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -285,9 +368,10 @@ def run_reference(args):
             "config": config_of(w, args, world),
             "cpu_baseline": {"value": value, "unit": "atom-evals/s", "cores": O.threads(),
                              "kind": "oracle",
-                             "sample": (f"each step: FP64 oracle grid part for all {w.N} atoms "
-                                        f"(mean {statistics.mean(tg):.2f} s) + local part for "
-                                        f"{S} random atoms, extrapolated to all {w.N}")},
+                             "sample": (f"each step one full FP64 oracle evaluation of all "
+                                        f"{w.N} atoms on all cores"),
+                             "single_thread": {"value": w.N / t_one, "cores": 1,
+                                               "sample": how}},
             "e2e": {"value": value, "unit": "atom-evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -295,16 +379,13 @@ def run_reference(args):
 
 
 def run_reference_batch(args):
-    """Oracle arm of the batched workload: each step times the FP64 oracle on
-    one replica (cycling through the replicas by size rank), grid part in full
-    and local part on a 1/32 sample, and reports atoms per second."""
+    """Oracle arm of the batched workload: each step is one full FP64 oracle
+    evaluation of one replica (cycling through the replicas by size rank)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import dataclasses
-
-    import numpy as np
 
     from oracle import oracle as O
     from paper_1308_4005_gb300 import inputs as I
@@ -313,20 +394,17 @@ def run_reference_batch(args):
     ws = I.batch_workloads(B=nrep)
     O.build()
     O.set_threads(os.cpu_count() or 1)
-    rng = np.random.default_rng(11)
     order = sorted(range(nrep), key=lambda r: ws[r].N)
     picks = [order[(k * nrep) // max(1, args.steps + args.warmup)]
              for k in range(args.steps + args.warmup)]
     atoms = secs = 0.0
     for k, r in enumerate(picks):
-        w = ws[r]
-        w = dataclasses.replace(w, levels=I_auto_levels(w))
+        w = dataclasses.replace(ws[r], levels=I_auto_levels(ws[r]))
         x, c = I.generate(w)
-        S = min(w.N, max(1, w.N // 32))
-        t_grid, t_loc = _oracle_parts(O, w, x, c, S, rng)
+        t = oracle_full(O, w, x, c)
         if k >= args.warmup:
             atoms += w.N
-            secs += t_grid + t_loc * w.N / S
+            secs += t
     value = atoms / secs
     line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -336,9 +414,8 @@ def run_reference_batch(args):
                        "h": ws[0].h, "levels": "auto per replica"},
             "cpu_baseline": {"value": value, "unit": "atom-evals/s", "cores": O.threads(),
                              "kind": "oracle",
-                             "sample": (f"each step: one replica (spread over the size range), "
-                                        "FP64 oracle grid part in full + local part for 1/32 "
-                                        "of its atoms, extrapolated")},
+                             "sample": ("each step one full FP64 oracle evaluation of one "
+                                        "replica (spread over the size range)")},
             "e2e": {"value": value, "unit": "atom-evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -359,7 +436,282 @@ def config_of(w, args, world):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+# ----------------------------------------------------------- roofline
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, 1900.0, "of fallback"
+
+
+def stage_work(info, N, n_pairs, prec, vir):
+    """Algorithmic work of one launch of every stage: (bound, amount, unit,
+    what is counted).  Bytes are the data each stage must move at least
+    once; flops follow the fixed tallies above."""
+    esz = 8 if prec == "fp64" else 4
+    lv = info["n_grid"]
+    np_ = [n[0] * n[1] * n[2] for n in lv]
+    l = len(lv)
+    fp_pair = FLOP_PAIR + (FLOP_PAIR_VIR if vir else 0)
+    fp_tap = FLOP_TAP + (FLOP_TAP_VIR if vir else 0)
+    fx = 8 if prec == "fp64" else 4  # fixed-point sums
+    w = {
+        "bin": ("hbm", N * 80.0, "B", "per atom: input 16 B read, record 16 B + cell 4 B "
+                "written, scatter 20 B read + 20 B written, order 4 B"),
+        "pair": ("alu", n_pairs * float(fp_pair), "flop",
+                 f"{n_pairs} ordered pairs inside a x {fp_pair} flop"),
+        "anterpolate": ("hbm", N * 16.0 + np_[0] * (2.0 * fx + esz), "B",
+                        "per atom: sorted record; finest grid: fixed-point sums written and "
+                        "read once, q^1 written"),
+        "restrict": ("hbm", sum((np_[k] + np_[k + 1]) * esz for k in range(l - 1)) * 1.0, "B",
+                     "every level k < l read once, level k+1 written"),
+        "stencil": ("alu", sum(np_[:-1]) * float(info["ntaps"]) * fp_tap, "flop",
+                    f"{sum(np_[:-1])} nodes on levels < l x {info['ntaps']} taps x {fp_tap} flop"),
+        "coarsest": ("alu64", np_[-1] ** 2 * float(2 + (12 if vir else 0)), "flop",
+                     f"{np_[-1]}^2 node pairs of the coarsest table"),
+        "prolongate": ("hbm", sum((np_[k + 1] + 2 * np_[k]) * esz for k in range(l - 1)) * 1.0,
+                       "B", "e^{k+1,tot} and e^k read, e^{k,tot} written per level"),
+        "interpolate": ("hbm", N * (16.0 + 4 + 7 * esz) + np_[0] * esz, "B",
+                        "per atom: sorted record, index, e0 + local force in, force out; "
+                        "finest grid once"),
+    }
+    return w
+
+
+def rooflines(stage_ms, work, peaks, prec, stencil_kind, workload, vir):
+    """One entry per stage: achieved rate (algorithmic work / stage time)
+    against the stage's peak."""
+    hbm, bf16, hbm_src = peaks["hbm"], peaks["bf16"], peaks["src"]
+    out = {}
+    for st, (bound, amount, unit, note) in work.items():
+        ms = stage_ms.get(st)
+        if not ms:
+            continue
+        if bound == "hbm":
+            ach, pk, u, src = amount / (ms * 1e-3) / 1e9, hbm, "GB/s", f"hbm_gbs {hbm_src}"
+        elif bound == "alu64" or (bound == "alu" and prec == "fp64"):
+            ach, pk, u, src = (amount / (ms * 1e-3) / 1e12, peaks["fp64"], "TFLOP/s",
+                               "FP64 FMA rate measured in this run (mls6_fma_peak)")
+            bound = "alu"
+        elif st == "stencil" and stencil_kind == 2:
+            ach, pk, u, src = (amount / (ms * 1e-3) / 1e12, bf16, "TFLOP/s",
+                               f"bf16_tflops {hbm_src}: useful flops of BF16 split products")
+            bound = "tensor"
+        else:
+            ach, pk, u, src = (amount / (ms * 1e-3) / 1e12, peaks["fp32"], "TFLOP/s",
+                               "FP32 FMA rate measured in this run (mls6_fma_peak)")
+        tr = None if not vir else TRAFFIC.get((workload, prec, st))
+        out[st] = {"bound": bound, "achieved": ach, "peak": pk, "unit": u, "frac": ach / pk,
+                   "traffic": tr, "work": note, "peak_source": src, "avg_launch_ms": ms}
+    return out
+
+
 # ------------------------------------------------------------------ ours
+
+def timed_steps(torch, stream, step, steps, flush, world=1):
+    """CUDA-event time (ms) of each of `steps` calls of step(), the L2
+    flushed (256 MiB write) before each."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+class Bench:
+    """Device buffers and one plan of a workload."""
+
+    def __init__(self, torch, mls6, dev, stream, box, N, a, h, levels, prec, x, c, vir=True):
+        import numpy as np
+
+        self.torch, self.mls6, self.stream = torch, mls6, stream
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        self.N, self.prec = N, prec
+        self.plan = mls6.Plan(box, N, a, h, levels, precision=prec, stream=stream.cuda_stream)
+        self.info = self.plan.info()
+        self.pos_h = torch.tensor(np.c_[x, c], dtype=dt).pin_memory()
+        self.pos = torch.empty((N, 4), dtype=dt, device=dev)
+        self.F = torch.empty((N, 3), dtype=dt, device=dev)
+        self.F_h = torch.empty((N, 3), dtype=dt).pin_memory()
+        self.out = torch.zeros(8, dtype=torch.float64, device=dev)
+        self.out_h = torch.zeros(8, dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
+            self.pos.copy_(self.pos_h, non_blocking=True)
+        stream.synchronize()
+        self.vir_ptr = self.out.data_ptr() + 8 if vir else 0
+
+    def step(self):
+        rc = self.mls6.mls6_eval(self.plan.handle, self.pos.data_ptr(), 0, self.F.data_ptr(),
+                                 self.out.data_ptr(), self.vir_ptr)
+        if rc:
+            raise self.mls6.MLS6Error(rc, "mls6_eval")
+
+    def e2e_step(self):
+        self.pos.copy_(self.pos_h, non_blocking=True)
+        self.step()
+        self.F_h.copy_(self.F, non_blocking=True)
+        self.out_h.copy_(self.out, non_blocking=True)
+
+    def warm(self, n, dwell=0.0):
+        with self.torch.cuda.stream(self.stream):
+            for _ in range(n):
+                self.step()
+            self.stream.synchronize()
+            t_end = time.time() + dwell
+            while time.time() < t_end:
+                for _ in range(20):
+                    self.step()
+                self.stream.synchronize()
+        rc = self.mls6.mls6_last_error(self.plan.handle)
+        if rc:
+            raise self.mls6.MLS6Error(rc, "warm-up")
+
+    def stages(self, steps, flush):
+        """Per-stage CUDA-event times (ms), stages serialised."""
+        mls6 = self.mls6
+        mls6.mls6_profile(self.plan.handle, True)
+        acc = {}
+        with self.torch.cuda.stream(self.stream):
+            for k in range(steps):
+                flush.fill_(k & 0xFF)
+                self.step()
+                st, _ = mls6.mls6_stage_times(self.plan.handle)
+                for name, ms in st.items():
+                    acc[name] = acc.get(name, 0.0) + ms
+        mls6.mls6_profile(self.plan.handle, False)
+        return {k: v / steps for k, v in acc.items()}
+
+    def forces(self):
+        self.torch.cuda.synchronize()
+        return self.F.double().cpu().numpy()
+
+    def close(self):
+        self.plan.close()
+
+
+def form_point(torch, mls6, dev, stream, flush, w, x, c, prec, a, h, levels, idx, Fex, steps):
+    """Throughput and eps_F of one form at one (a, h)."""
+    b = Bench(torch, mls6, dev, stream, w.box, w.N, a, h, levels, prec, x, c)
+    try:
+        b.warm(3)
+        ms = statistics.mean(timed_steps(torch, stream, b.step, steps, flush))
+        e = eps_F(b.forces()[idx], Fex)
+        return {"a": a, "h": h, "levels": b.info["levels"], "ms": ms, "value": w.N / (ms / 1e3),
+                "eps_F": e, "stencil_kind": b.info["stencil_kind"]}
+    finally:
+        b.close()
+
+
+def learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, steps, log):
+    """The learned correction at cutoff a: coarse evaluation (h = 2) plus the
+    network, trained on two 32,768-atom cubes of the same density against
+    the fine (h = 1) evaluation; eps_F, throughput, and the measured floor
+    (network time per atom against the grid time the coarse grid saves)."""
+    from paper_1308_4005_gb300 import inputs as I
+    from paper_1308_4005_gb300 import learn
+
+    st = learn.Setup(a=a)
+    t0 = time.time()
+    rho = w.N / (w.box[0] * w.box[1] * w.box[2])
+    train = []
+    for s in range(2):
+        tw = I.scaled_cube(32768, rho, a, 1.0, 0, 9300 + s)
+        tx, tc = I.generate(tw)
+        train.append((tw.box, tx, tc))
+    model, hist = learn.build_model(st, train, steps=800, batch=16384, lr=2e-3)
+    t_train = time.time() - t0
+    b = Bench(torch, mls6, dev, stream, w.box, w.N, a, st.h_coarse, 0, "fp32", x, c)
+    try:
+        b.warm(2)
+        ms_coarse = statistics.mean(timed_steps(torch, stream, b.step, steps, flush))
+
+        def step():
+            b.step()
+            model.apply(b.plan, b.F)
+
+        with torch.cuda.stream(stream):
+            step()
+        Fl = b.forces()
+        ms = statistics.mean(timed_steps(torch, stream, step, steps, flush))
+        net = statistics.mean(timed_steps(torch, stream, lambda: model.apply(b.plan, b.F),
+                                          steps, flush))
+        e = eps_F(Fl[idx], Fex)
+        with torch.cuda.stream(stream):
+            b.step()
+        e_c = eps_F(b.forces()[idx], Fex)
+        return {"a": a, "h": st.h_coarse, "ms": ms, "value": w.N / (ms / 1e3), "eps_F": e,
+                "eps_F_coarse_alone": e_c, "ms_coarse_alone": ms_coarse,
+                "ms_network": net, "train_s": t_train,
+                "train_loss": [float(hist[0]), float(hist[-1])]}
+    finally:
+        b.close()
+        model.close()
+
+
+def batch_point(torch, mls6, dev, stream, flush, ws, x, c, off, a, steps, tune):
+    """The batched replicas at cutoff a (h = 1, levels by the automatic
+    rule): one graph launch per step over every replica; eps_F on sampled
+    atoms of two cube and two slab replicas against exact forces."""
+    import numpy as np
+
+    Ntot = int(off[-1])
+    t0 = time.time()
+    bt = mls6.Batch([w.box for w in ws], [w.N for w in ws], a, ws[0].h, 0, precision="fp32")
+    t_plan = time.time() - t0
+    try:
+        mls6.mls6_batch_set_stream(bt.handle, stream.cuda_stream)
+        pos = torch.tensor(np.c_[x, c], dtype=torch.float32, device=dev)
+        F = torch.empty((Ntot, 3), dtype=torch.float32, device=dev)
+        E = torch.zeros(len(ws), dtype=torch.float64, device=dev)
+        W = torch.zeros((len(ws), 6), dtype=torch.float64, device=dev)
+        t_tune = None
+        if tune:
+            t0 = time.time()
+            with torch.cuda.stream(stream):
+                bt.tune(pos, reps=3)
+            t_tune = time.time() - t0
+
+        def step():
+            rc = mls6.mls6_batch_eval(bt.handle, pos.data_ptr(), 0, F.data_ptr(), E.data_ptr(),
+                                      W.data_ptr())
+            if rc:
+                raise mls6.MLS6Error(rc, "mls6_batch_eval")
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step()
+        ms = statistics.mean(timed_steps(torch, stream, step, steps, flush))
+        torch.cuda.synchronize()
+        Fb = F.double().cpu().numpy()
+        info = bt.info()
+        rng = np.random.default_rng(17)
+        picks = [r for r in range(0, len(ws), 2)][:2] + [r for r in range(1, len(ws), 2)][:2]
+        num = den = 0.0
+        for r in picks:
+            sl = slice(int(off[r]), int(off[r + 1]))
+            ii = rng.choice(ws[r].N, min(256, ws[r].N), replace=False)
+            Fex = exact_forces(x[sl], c[sl], ws[r].box, ii)
+            num += float(np.sum((Fb[sl][ii] - Fex) ** 2))
+            den += float(np.sum(Fex ** 2))
+        return {"a": a, "h": ws[0].h, "ms": ms, "value": Ntot / (ms / 1e3),
+                "eps_F": math.sqrt(num / den), "replicas": len(ws), "atoms": Ntot,
+                "launches_per_step": int(info["launches"]), "branches": info["branches"],
+                "plan_s": t_plan, "autotune_s": t_tune,
+                "eps_F_sample": "256 atoms of each of replicas " + ", ".join(map(str, picks))}
+    finally:
+        bt.close()
+
 
 def run_ours(args):
     import numpy as np
@@ -374,170 +726,125 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     B.build()
     mls6.load()
+    log = (lambda m: print(f"[bench] {m}", file=sys.stderr, flush=True)) if rank == 0 else \
+        (lambda m: None)
+    t_start = time.time()
     w, x, c = workload_arrays(args.workload, rank, args.precision)
-    dt = torch.float64 if args.precision == "fp64" else torch.float32
-    esz = 8 if args.precision == "fp64" else 4
+    log(f"inputs {w.name} in {time.time() - t_start:.1f} s")
+    vir = not args.no_virial
     N = w.N
     stream = torch.cuda.Stream(device=dev)
-    plan = mls6.Plan(w.box, N, w.a, w.h, w.levels, precision=args.precision,
-                     stream=stream.cuda_stream)
-    info = plan.info()
-    pos_h = torch.tensor(np.c_[x, c], dtype=dt).pin_memory()
-    pos = torch.empty((N, 4), dtype=dt, device=dev)
-    F = torch.empty((N, 3), dtype=dt, device=dev)
-    F_h = torch.empty((N, 3), dtype=dt).pin_memory()
-    out = torch.zeros(8, dtype=torch.float64, device=dev)
-    out_h = torch.zeros(8, dtype=torch.float64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    with torch.cuda.stream(stream):
-        pos.copy_(pos_h, non_blocking=True)
-    stream.synchronize()
+    hbm, bf16, src = load_peaks()
+    peaks = {"fp32": mls6.mls6_fma_peak("fp32"), "fp64": mls6.mls6_fma_peak("fp64"),
+             "hbm": hbm, "bf16": bf16, "src": src}
+    log(f"measured FMA peaks: FP32 {peaks['fp32']:.1f}, FP64 {peaks['fp64']:.2f} TFLOP/s")
 
-    vir_ptr = 0 if args.no_virial else out.data_ptr() + 8
-
-    def step():
-        rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), out.data_ptr(),
-                            vir_ptr)
-        if rc:
-            raise mls6.MLS6Error(rc, "mls6_eval")
-
+    b = Bench(torch, mls6, dev, stream, w.box, N, w.a, w.h, w.levels, args.precision, x, c, vir)
+    info = b.info
     sampler = ClockSampler(gpu_smi_id(torch, local))
     t_dwell0 = time.time()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.fill_(1)
-            step()
-        stream.synchronize()
-        t_end = time.time() + args.dwell
-        while time.time() < t_end:
-            for _ in range(50):
-                step()
-            stream.synchronize()
-    rc = mls6.mls6_last_error(plan.handle)
-    if rc:
-        raise mls6.MLS6Error(rc, "warmup")
+    b.warm(args.warmup, args.dwell)
 
     # ------------------------------------------------ timed region (device)
     # Production path: captured graph, pair sum concurrent with the grid
     # chain, no per-stage events.  L2 flushed before every step.
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    _, launches_per_step = mls6.mls6_stage_times(plan.handle)
-    launches = launches_per_step * args.steps
-    value, total_ms = job_throughput(torch, sum(a.elapsed_time(b) for a, b in ev), N,
-                                     args.steps, world, dev)
+    ms_list = timed_steps(torch, stream, b.step, args.steps, flush, world)
+    _, launches_per_step = mls6.mls6_stage_times(b.plan.handle)
+    value, total_ms = job_throughput(torch, sum(ms_list), N, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    E_dev = float(out[0].item())
-
-    # ------------------------------------- per-kernel times (serialised pass)
-    # Same steps with per-stage CUDA events on the launching stream; stages
-    # run one after another so each event pair times one stage alone.
-    mls6.mls6_profile(plan.handle, True)
-    stage_acc = {}
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            step()
-            st, _ = mls6.mls6_stage_times(plan.handle)  # waits for this step
-            for name, ms in st.items():
-                stage_acc[name] = stage_acc.get(name, 0.0) + ms
-    mls6.mls6_profile(plan.handle, False)
-    stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
-
-    # --------------------------------------------- end-to-end (host buffers)
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            ev2[k][0].record(stream)
-            pos.copy_(pos_h, non_blocking=True)
-            step()
-            F_h.copy_(F, non_blocking=True)
-            out_h.copy_(out, non_blocking=True)
-            ev2[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    e2e_value, _ = job_throughput(torch, sum(a.elapsed_time(b) for a, b in ev2), N, args.steps,
-                                  world, dev)
-    t_e2e1 = time.time()
+    E_dev = float(b.out[0].item())
+    # --------------------------------------------- end to end (host buffers)
+    ms2 = timed_steps(torch, stream, b.e2e_step, args.steps, flush, world)
+    e2e_value, _ = job_throughput(torch, sum(ms2), N, args.steps, world, dev)
+    t_timed1 = time.time()
     sampler.stop()
-    clocks = sampler.summary(t_dwell0, t_e2e1)
-    clocks["window"] = "warm-up dwell + timed steps (the timed region alone is shorter than the sampling period)"
+    clocks = sampler.summary(t_dwell0, t_timed1)
+    clocks["window"] = "warm-up dwell + timed steps"
+    # ------------------------------------- per-kernel times (serialised pass)
+    stage_ms = b.stages(args.steps, flush)
+    F_main = b.forces()
+    b.close()
 
     # ------------------------------------------------------------- roofline
-    n_pairs = count_pairs(x, np.array(w.box), w.a)
-    lv = info["n_grid"]
-    nodes_lt = sum(n[0] * n[1] * n[2] for n in lv[:-1])
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    fp_pair = FLOP_PAIR + (0 if args.no_virial else FLOP_PAIR_VIR)
-    fp_tap = FLOP_TAP + (0 if args.no_virial else FLOP_TAP_VIR)
-    work = {
-        "pair": ("alu", n_pairs * fp_pair / 1e12, "TFLOP/s",
-                 f"{n_pairs} ordered pairs inside a x {fp_pair} flop"),
-        "stencil": ("alu", nodes_lt * info["ntaps"] * fp_tap / 1e12,
-                    "TFLOP/s", f"{nodes_lt} nodes on levels < l x {info['ntaps']} taps x "
-                               f"{fp_tap} flop"),
-        "interpolate": ("hbm", (N * (16 + 4 + esz + 3 * esz + 3 * esz) + lv[0][0] * lv[0][1] *
-                                lv[0][2] * esz) / 1e9, "GB/s",
-                        "per atom: sorted record, index, e0, local force in, force out; grid once"),
-        "anterpolate": ("hbm", (N * 16 + lv[0][0] * lv[0][1] * lv[0][2] * esz) / 1e9, "GB/s",
-                        "per atom: sorted record; finest grid written once"),
-        "bin": ("hbm", N * (16 + 16 + 4 + 4 + 16 + 4 + 16 + 4) / 1e9, "GB/s",
-                "read input, write wrapped record + cell id, scatter read/write, sort"),
-    }
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    roof = None
-    if dom in work:
-        bound, amount, unit, note = work[dom]
-        ach = amount / (stage_ms[dom] / 1e3)
-        if dom == "stencil" and info.get("stencil_kind") == 2:
-            bound, peak = "tensor", tensor_peak()
-            peak_note = ("MEASURED_PEAKS.json bf16_tflops (of measured; cuBLAS bf16 burst): the "
-                         "stencil runs as BF16 mma with split operands")
-        if bound == "tensor":
-            pass
-        elif bound == "alu":
-            peak, peak_note = fp32_peak, (f"FP32 FMA peak derived: {SMS} SMs x "
-                                          f"{FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz "
-                                          "(median sampled SM clock)")
-        else:
-            peak, peak_note = hbm_peak(), "MEASURED_PEAKS.json hbm_gbs (of measured)"
-        traffic = None if args.no_virial else TRAFFIC.get((w.name, args.precision, dom))
-        roof = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                "frac": ach / peak, "traffic": traffic, "work": note, "peak_source": peak_note,
-                "avg_launch_ms": stage_ms[dom],
-                "timing": ("CUDA events on the launching stream around the stage, averaged over "
-                           "a serialised pass of the same steps right after the timed region")}
+    n_pairs = count_pairs(x, w.box, w.a)
+    work = stage_work(info, N, n_pairs, args.precision, vir)
+    roofs = rooflines(stage_ms, work, peaks, args.precision, info["stencil_kind"], w.name, vir)
+    dom = max(roofs, key=lambda k: roofs[k]["avg_launch_ms"])
+    roof = dict(roofs[dom], kernel=dom,
+                timing=("CUDA events on the launching stream around the stage, averaged over a "
+                        "serialised pass of the same steps right after the timed region"))
+    if dom == "stencil" and info["stencil_kind"] == 2:
+        roof["issued_over_useful"] = "32/13 Toeplitz band x 3 split products (energy channel)"
     line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": config_of(w, args, world),
             "e2e": {"value": e2e_value, "unit": "atom-evals/s",
-                    "h2d_bytes_per_step": int(pos_h.numel() * pos_h.element_size()),
-                    "d2h_bytes_per_step": int(F_h.numel() * F_h.element_size() + 8 * 8)},
-            "gpu_launches": int(launches),
-            "roofline": roof, "stages_ms": stage_ms, "clocks": clocks,
-            "energy": E_dev}
+                    "h2d_bytes_per_step": int(b.pos_h.numel() * b.pos_h.element_size()),
+                    "d2h_bytes_per_step": int(b.F_h.numel() * b.F_h.element_size() + 8 * 8)},
+            "gpu_launches": int(launches_per_step) * args.steps,
+            "roofline": roof, "roofline_stages": roofs, "stages_ms": stage_ms,
+            "peaks": {k: v for k, v in peaks.items()}, "clocks": clocks, "energy": E_dev}
+
+    extras = rank == 0 and world == 1 and not args.quick and w.name == "cube1m"
+    if extras:
+        rng = np.random.default_rng(5)
+        idx = rng.choice(N, 2048, replace=False)
+        t0 = time.time()
+        Fex = exact_forces(x, c, w.box, idx)
+        log(f"exact forces on {idx.size} sampled atoms in {time.time() - t0:.1f} s")
+        line["eps_F"] = eps_F(F_main[idx], Fex)
+        line["accuracy"] = {
+            "eps_F": "||F - F_exact|| / ||F_exact|| over all components of 2048 sampled atoms",
+            "F_exact": (f"direct periodic sum of c_i c_j r^-6 over every image within "
+                        f"{EXACT_R} sigma"),
+            "target": TARGET_EPS}
+        sweep = {"fp32": [], "mixed": []}
+        for a in (3.0, 3.5, 4.0):
+            for prec in ("fp32", "mixed"):
+                try:
+                    sweep[prec].append(form_point(torch, mls6, dev, stream, flush, w, x, c, prec,
+                                                  a, w.h, w.levels, idx, Fex, 10))
+                except Exception as e:  # report, keep the main line
+                    sweep[prec].append({"a": a, "error": repr(e)})
+        log(f"sweep done at {time.time() - t_start:.0f} s")
+        line["forms"] = {p: dict(v[0]) for p, v in sweep.items() if v and "value" in v[0]}
+        line["sweep"] = sweep
+        at = {p: at_target(v) for p, v in sweep.items()}
+        try:
+            lp = [learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, 10, log)
+                  for a in (3.0, 3.5)]
+            line["learned"] = lp
+            at["learned"] = at_target(lp)
+        except Exception as e:
+            line["learned"] = {"error": repr(e)}
+        log(f"learned done at {time.time() - t_start:.0f} s")
+        try:
+            from paper_1308_4005_gb300 import inputs as I
+
+            ws = I.batch_workloads(B=256)
+            t0 = time.time()
+            bx, bc, off = I.generate_batch(ws, processes=min(16, os.cpu_count() or 1))
+            bx, bc = bx.astype(np.float32), bc.astype(np.float32)
+            t_gen = time.time() - t0
+            bp = [batch_point(torch, mls6, dev, stream, flush, ws, bx, bc, off, a, 10,
+                              not args.no_tune) for a in (2.5, 3.5)]
+            bp[0]["generate_s"] = t_gen
+            line["batched"] = bp
+            at["batched"] = at_target(bp)
+        except Exception as e:
+            line["batched"] = {"error": repr(e)}
+        log(f"batched done at {time.time() - t_start:.0f} s")
+        line["at_1e-4"] = at
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.time()
         line["cpu_baseline"] = oracle_baseline(w, x, c)
+        log(f"oracle baseline in {time.time() - t0:.1f} s")
+    line["wall_s"] = time.time() - t_start
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         import torch.distributed as dist
 
@@ -673,8 +980,7 @@ def run_batch(args):
         work_sten += sum(n[0] * n[1] * n[2] for n in lv[:-1]) * pinfo["ntaps"] * \
             (FLOP_TAP + FLOP_TAP_VIR)
     dom = max(stage_acc, key=lambda k: stage_acc[k])
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fp32_peak = mls6.mls6_fma_peak("fp32")
     roof = None
     if dom in ("pair", "stencil"):
         amount = (work_pair if dom == "pair" else work_sten) / 1e12
@@ -682,8 +988,7 @@ def run_batch(args):
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
                 "work": f"sum over the {nrep} replicas of the {dom} kernel's algorithmic flops",
-                "peak_source": (f"FP32 FMA peak derived: {SMS} SMs x {FP32_LANES_PER_SM} lanes "
-                                f"x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)"),
+                "peak_source": "FP32 FMA rate measured in this run (mls6_fma_peak)",
                 "avg_launch_ms": stage_acc[dom] / nrep,
                 "timing": ("CUDA events around the stage, each replica's plan evaluated alone "
                            "with serialised stages after the timed region")}
@@ -725,207 +1030,8 @@ def run_batch(args):
     return 0
 
 
-# ------------------------------------------- throughput at equal accuracy
-
-def _timed_evals(fn, steps, warmup, stream):
-    import torch
-
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            fn()
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps
-
-
-def run_accuracy(args):
-    """Force error against a converged reference and throughput of the plain
-    FP32, mixed-precision and learned forms over a cutoff sweep on a held-out
-    slab (proportions of the 4,194,304-atom slab), and the throughput of
-    each form interpolated (log-log) at eps_F = 1e-4."""
-    import numpy as np
-    import torch
-
-    from paper_1308_4005_gb300 import build as B
-    from paper_1308_4005_gb300 import learn
-    from paper_1308_4005_gb300 import mls6
-
-    world, rank, local = dist_setup(torch)
-    torch.cuda.set_device(local)
-    B.build()
-    mls6.load()
-    N = 1048576 if args.workload == "accuracy" else 65536
-    box, x, c = learn.slab_system(N, 7000 + rank)
-    stream = torch.cuda.Stream()
-    ref = learn.Setup()
-    _, _, Fref = learn._forces(box, x, c, ref.a_ref, ref.h_ref, "fp32")
-    cuts = [3.0, 3.5, 4.0] if args.workload == "accuracy" else [3.0, 3.5]
-    res = {"fp32": [], "mixed": [], "learned": []}
-    pos32 = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
-    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
-    for a in cuts:
-        for form in ("fp32", "mixed"):
-            plan = mls6.Plan(box, N, a, 1.0, 0, precision=form, stream=stream.cuda_stream)
-            r = plan.evaluate(pos32, virial=False)
-            torch.cuda.synchronize()
-            eps = learn.eps_F(r["F"], Fref)
-            ms = _timed_evals(lambda: mls6.mls6_eval(plan.handle, pos32.data_ptr(), 0,
-                                                     F.data_ptr(), 0, 0), 20, 3, stream)
-            res[form].append({"a": a, "h": 1.0, "eps_F": eps, "ms": ms, "value": N / (ms / 1e3)})
-            plan.close()
-        st = learn.Setup(a=a)
-        train = [learn.slab_system(32768, 9000 + 10 * int(4 * a) + s) for s in range(2)]
-        model, hist = learn.build_model(st, train, steps=800, batch=16384, lr=2e-3)
-        plan = mls6.Plan(box, N, a, st.h_coarse, 0, precision="fp32", stream=stream.cuda_stream)
-        r = plan.evaluate(pos32, virial=False)
-        torch.cuda.synchronize()  # the plan runs on its own stream
-        Fl = r["F"].clone()
-        torch.cuda.synchronize()
-        model.apply(plan, Fl)
-        torch.cuda.synchronize()
-        eps_c = learn.eps_F(r["F"], Fref)
-        eps = learn.eps_F(Fl, Fref)
-
-        def learned_step():
-            mls6.mls6_eval(plan.handle, pos32.data_ptr(), 0, F.data_ptr(), 0, 0)
-            model.apply(plan, F)
-
-        ms = _timed_evals(learned_step, 20, 3, stream)
-        res["learned"].append({"a": a, "h": st.h_coarse, "eps_F": eps, "eps_F_coarse": eps_c,
-                               "ms": ms, "value": N / (ms / 1e3), "train_loss": hist[-1]})
-        model.close()
-        plan.close()
-
-    def at(points, target=1e-4):
-        pts = sorted(points, key=lambda p: p["eps_F"])
-        le = np.log([p["eps_F"] for p in pts])
-        lv = np.log([p["value"] for p in pts])
-        t = np.log(target)
-        if len(pts) < 2:
-            return None, "one point"
-        j = int(np.clip(np.searchsorted(le, t), 1, len(pts) - 1))
-        f = (t - le[j - 1]) / (le[j] - le[j - 1])
-        how = "interpolated" if le[0] <= t <= le[-1] else "extrapolated"
-        return float(np.exp(lv[j - 1] + f * (lv[j] - lv[j - 1]))), how
-
-    at_target = {k: at(v) for k, v in res.items()}
-    line = {"metric": "atom-evals/s at eps_F = 1e-4", "value": at_target["mixed"][0],
-            "unit": "atom-evals/s", "n_gpus": world, "steps": 20, "warmup": 3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+bf16x3", "data": "synthetic",
-            "config": {"workload": f"slab{N} (proportions of the 4,194,304-atom slab)",
-                       "reference": f"FP32 MLS a={ref.a_ref}, h={ref.h_ref}",
-                       "virial": False, "cutoffs": cuts,
-                       "learned": "coarse h=2 + network trained on h=1 targets per cutoff"},
-            "at_1e-4": {k: {"value": v[0], "how": v[1]} for k, v in at_target.items()},
-            "sweep": res}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_learned(args):
-    """The 4,194,304-atom slab (160 x 160 x 240, a = 3): throughput of the fine
-    evaluation (h = 1), the coarse one (h = 2) and the coarse one plus the
-    learned correction (network trained first on two 32,768-atom slabs of the
-    same proportions).  Forces only (no virial), FP32."""
-    import numpy as np
-    import torch
-
-    from paper_1308_4005_gb300 import build as B
-    from paper_1308_4005_gb300 import learn
-    from paper_1308_4005_gb300 import mls6
-
-    world, rank, local = dist_setup(torch)
-    torch.cuda.set_device(local)
-    B.build()
-    mls6.load()
-    st = learn.Setup()
-    t0 = time.time()
-    train = [learn.slab_system(32768, 9100 + s) for s in range(2)]
-    model, hist = learn.build_model(st, train, steps=800, batch=16384, lr=2e-3)
-    t_train = time.time() - t0
-    N = 4194304 if args.workload == "learned4m" else 262144
-    t0 = time.time()
-    box, x, c = learn.slab_system(N, 9200 + rank)
-    t_gen = time.time() - t0
-    stream = torch.cuda.Stream()
-    pos = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
-    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {}
-    for name, h, learned in (("fine", st.h_fine, False), ("coarse", st.h_coarse, False),
-                             ("learned", st.h_coarse, True)):
-        plan = mls6.Plan(box, N, st.a, h, 0, precision="fp32", stream=stream.cuda_stream)
-
-        def step():
-            flush.fill_(1)
-            rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), 0, 0)
-            if rc:
-                raise mls6.MLS6Error(rc, "mls6_eval")
-            if learned:
-                model.apply(plan, F)
-
-        ev = []
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                step()
-            stream.synchronize()
-            for _ in range(args.steps):
-                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                flush.fill_(2)
-                a_.record(stream)
-                rc = mls6.mls6_eval(plan.handle, pos.data_ptr(), 0, F.data_ptr(), 0, 0)
-                if learned:
-                    model.apply(plan, F)
-                b_.record(stream)
-                ev.append((a_, b_))
-        torch.cuda.synchronize()
-        ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / len(ev)
-        out[name] = {"h": h, "ms": ms, "value": N / (ms / 1e3),
-                     "levels": plan.info()["levels"], "grid": plan.info()["n_grid"][0]}
-        plan.close()
-    line = {"metric": "atom-evals/s", "value": out["learned"]["value"], "unit": "atom-evals/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": out["learned"]["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
-            "config": {"workload": f"slab{N} (160x160x240 proportions)", "a": st.a,
-                       "virial": False, "train_s": t_train, "generate_s": t_gen,
-                       "train_loss": [hist[0], hist[-1]],
-                       "l2": "flushed between timed steps (256 MiB write)"},
-            "forms": out}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
-
-
-def tensor_peak():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
-    except Exception:
-        return 1900.0
-
-
-def hbm_peak():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except Exception:
-        return 6800.0
-
-
 def main():
     args = parse()
-    if args.workload.startswith("accuracy"):
-        return run_accuracy(args)
-    if args.workload.startswith("learned"):
-        return run_learned(args)
     if args.workload.startswith("batch"):
         if args.impl == "reference":
             return run_reference_batch(args)

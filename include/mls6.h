@@ -86,13 +86,28 @@ int mls6_grid_dims(const double box[3], double h, int levels, int n_out[3]);
 int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double a, double* T,
                        double* V);
 
-/* Create a plan: validates the parameters, computes the grid hierarchy and
- * every table on the host in FP64, and allocates all device workspace (the
- * plan owns it).  box: 3 doubles.  N: number of atoms (>= 0), fixed for the
- * plan.  a: local cutoff (> 0).  h: requested finest spacing (> 0).
- * levels: number of grid levels l (1..12), or 0 for the automatic rule of
- * mls6_auto_levels.  order: interpolation order, 3.
- * precision: mls6_precision.  *out receives the plan (NULL on error). */
+/* Create a plan: the set-up of the method's algorithmic steps (Sec. II.B)
+ * for one box and one atom count.  Validates the parameters, computes the
+ * nested grid hierarchy (Sec. II.A.4, spacing 2^(k-1) h on level k), the
+ * level-stencil table g_1(|m h_1|) for |m h_1| < 2a (Eq. g_k; the same table
+ * serves every level k < l, scaled by 2^(-6(k-1))), the coarsest-level
+ * periodic table (Eq. last-grid-periodic-transformed, Ewald-summed) and the
+ * self term gamma(0)/a^6 (Eq. self-interaction-energy), all on the host in
+ * FP64, and allocates all device workspace (the plan owns it).
+ *   box        3 doubles (Lx, Ly, Lz), host
+ *   N          number of atoms (>= 0), fixed for the plan
+ *   a          local cutoff (> 0), the split radius of Eq. (g_0)
+ *   h          requested finest spacing (> 0); the actual spacing per axis
+ *              is L/n_1 (mls6_grid_dims)
+ *   levels     number of grid levels l (1..12), or 0 for the automatic rule
+ *              of mls6_auto_levels
+ *   order      interpolation order p, 3 (Eq. Phi-Hermite); other values
+ *              return MLS6_ERR_ORDER
+ *   precision  an mls6_precision value, passed as a plain int (the ABI has
+ *              no options struct; the stream is set with mls6_set_stream)
+ *   *out       receives the plan (NULL on error)
+ * Errors: MLS6_ERR_ARG / _BOX / _GRID / _ORDER for bad parameters,
+ * MLS6_ERR_NOMEM / _CUDA for device failures; nothing is leaked. */
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision);
 
@@ -110,7 +125,11 @@ int mls6_set_stream(mls6_plan_t* p, void* stream);
  * kernels one by one. */
 int mls6_set_graph(mls6_plan_t* p, int enable);
 
-/* Evaluate energy, forces and virial.
+/* Evaluate energy, forces and virial: one pass of the method's five steps
+ * (Sec. II.B: anterpolation, restriction, evaluation on every level,
+ * prolongation, interpolation) plus the local pair sum of Eq. (g_0), i.e.
+ * the quadratic form of Eq. (pot-vec-mat-vec) with xi = c, split as in
+ * Eq. (pot-initial-splitting).
  *   pos     device pointer, N rows of the plan's precision (double or float):
  *           if c == NULL each row is {x, y, z, c} (4 values), otherwise
  *           {x, y, z} (3 values).  Positions may lie anywhere; they are
@@ -381,12 +400,24 @@ void mls6_mlp_destroy(mls6_mlp_t* m);
  * Its scratch (six doubles per node) is one fixed file-scope device array of
  * 192 KiB that every GPU loading the library holds until the process exits.
  * The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ * that first call before any stream capture.  A cudaDeviceReset (or
+ * anything else that destroys the device's primary context) invalidates
+ * the kept address: do not call this entry point on that device again in
+ * the same process.
  * All calls share the array and every entry a call reads is written by the
  * same call, so nothing needs clearing, but calls that overlap on the GPU
  * (different streams, or different host threads) race on it. */
 int mls6_coarse_apply_noalloc(const double* q, const int n[3], const double* T, const double* V,
                               double* e, double* virial, void* stream);
+
+/* Measured fused multiply-add rate of the current device (TFLOP/s, 2 flop
+ * per FMA): precision MLS6_FP32 or MLS6_FP64.  A measurement tool for the
+ * arithmetic rooflines of the pair and level-stencil kernels (the paper has
+ * no counterpart): every SM runs independent FMA chains for ~20 ms, best of
+ * five timed launches on the legacy default stream.  Synchronous; allocates
+ * and frees a small device buffer. */
+int mls6_fma_peak(int precision, double* tflops);
 
 /* Release the plan and all its device memory.  NULL is ignored. */
 void mls6_destroy(mls6_plan_t* p);

@@ -43,7 +43,7 @@ EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream
            "mls6_mlp_n_params", "mls6_mlp_create", "mls6_mlp_set_stream", "mls6_mlp_get_params",
            "mls6_mlp_set_params", "mls6_mlp_set_norm", "mls6_mlp_features", "mls6_mlp_forward",
            "mls6_mlp_grad", "mls6_mlp_train_step", "mls6_mlp_apply", "mls6_mlp_destroy",
-           "mls6_coarse_apply_noalloc", "mls6_destroy", "mls6_status_string")
+           "mls6_coarse_apply_noalloc", "mls6_fma_peak", "mls6_destroy", "mls6_status_string")
 
 _lib = None
 _dp = C.POINTER(C.c_double)
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
     L.mls6_coarse_apply_noalloc.argtypes = [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p]
     L.mls6_coarse_apply_noalloc.restype = C.c_int
+    L.mls6_fma_peak.argtypes = [C.c_int, _dp]
+    L.mls6_fma_peak.restype = C.c_int
     L.mls6_destroy.argtypes = [C.c_void_p]
     L.mls6_destroy.restype = None
     L.mls6_auto_levels.argtypes = [_dp, C.c_double]
@@ -166,6 +168,13 @@ def _check(rc, where):
 
 def _darr(vals):
     return (C.c_double * len(vals))(*[float(v) for v in vals])
+
+
+def mls6_fma_peak(precision):
+    """Measured FMA rate of the current device in TFLOP/s."""
+    v = C.c_double()
+    _check(load().mls6_fma_peak(_PREC[precision], C.byref(v)), "mls6_fma_peak")
+    return v.value
 
 
 def status_string(code: int) -> str:

@@ -1,0 +1,46 @@
+"""Host-side logic of the benchmark (no GPU): the exact sampled forces that
+define eps_F, the pair count behind the pair kernel's algorithmic work, and
+the equal-accuracy interpolation."""
+import numpy as np
+import pytest
+
+import bench
+from paper_1308_4005_gb300 import inputs as I
+
+
+def test_exact_forces_match_brute_force(orc):
+    """Direct image sums within R = 20 reproduce the oracle's brute-force
+    periodic forces (windowed image sum with its continuum tail), for a
+    small box (replicated images) and a box wider than 2R (minimum image)."""
+    box = (9.0, 10.0, 11.0)
+    x, c = I.uniform_atoms(3, 300, box)
+    idx = np.arange(0, 300, 7)
+    ref = orc.brute(box, x, c, r_img=8 * max(box))["F"]
+    Fe = bench.exact_forces(x, c, box, idx)
+    assert np.abs(Fe - ref[idx]).max() <= 1e-7 * np.abs(ref).max()
+    big = (42.0, 41.0, 43.0)
+    xb, cb = I.uniform_atoms(4, 400, big)
+    ib = np.arange(0, 400, 5)
+    refb = orc.brute(big, xb, cb, r_img=5 * max(big))["F"]
+    Fb = bench.exact_forces(xb, cb, big, ib)
+    assert np.abs(Fb - refb[ib]).max() <= 1e-6 * np.abs(refb).max()
+    assert bench.eps_F(Fb, refb[ib]) <= 1e-7
+
+
+def test_pair_count_is_ordered_pairs_inside_cutoff():
+    from scipy.spatial import cKDTree
+
+    box = (12.0, 13.0, 9.0)
+    x, _ = I.uniform_atoms(5, 800, box)
+    p = cKDTree(np.mod(x, box), boxsize=box).query_pairs(3.0, output_type="ndarray")
+    assert bench.count_pairs(x, box, 3.0) == 2 * len(p)
+
+
+def test_equal_accuracy_interpolation():
+    pts = [{"eps_F": 4e-4, "value": 8.0}, {"eps_F": 1.6e-3, "value": 16.0},
+           {"eps_F": 1e-4, "value": 4.0}]
+    r = bench.at_target(pts, 1e-4)
+    assert r["value"] == pytest.approx(4.0) and r["how"] == "interpolated"
+    r = bench.at_target(pts, 2e-4)  # halfway in log between 1e-4 and 4e-4
+    assert r["value"] == pytest.approx(4.0 * np.sqrt(2.0))
+    assert bench.at_target(pts[:2], 1e-4)["how"] == "extrapolated"

@@ -7,8 +7,10 @@ fixed file-scope device array.  This test runs a normal FP64 evaluation,
 takes the coarsest-level grid xi^l it produced, applies the allocation-free
 entry point to it twice in a row, and checks e^l against the grid the
 evaluation itself computed, and the virial term against the same quadratic
-form evaluated from the table in FP64 on the host.  It lives in a file of
-its own so that it runs after every other test.
+form evaluated from the table in FP64 on the host.  Each test builds
+everything it uses, so it passes alone, after the other tests, or in any
+order; it lives in a file that pytest collects last only so that, in a run
+that stops at the first failure, every other test has already run.
 """
 import ctypes as C
 
