@@ -496,7 +496,7 @@ def rooflines(stage_ms, work, peaks, prec, stencil_kind, workload, vir):
             ach, pk, u, src = (amount / (ms * 1e-3) / 1e12, peaks["fp64"], "TFLOP/s",
                                "FP64 FMA rate measured in this run (mls6_fma_peak)")
             bound = "alu"
-        elif st == "stencil" and stencil_kind == 2:
+        elif st == "stencil" and stencil_kind in (2, 3):
             ach, pk, u, src = (amount / (ms * 1e-3) / 1e12, bf16, "TFLOP/s",
                                f"bf16_tflops {hbm_src}: useful flops of BF16 split products")
             bound = "tensor"
@@ -774,7 +774,7 @@ def run_ours(args):
     roof = dict(roofs[dom], kernel=dom,
                 timing=("CUDA events on the launching stream around the stage, averaged over a "
                         "serialised pass of the same steps right after the timed region"))
-    if dom == "stencil" and info["stencil_kind"] == 2:
+    if dom == "stencil" and info["stencil_kind"] in (2, 3):
         roof["issued_over_useful"] = "32/13 Toeplitz band x 3 split products (energy channel)"
     line = {"metric": "atom-evals/s", "value": value, "unit": "atom-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

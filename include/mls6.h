@@ -56,7 +56,7 @@ typedef enum {
   MLS6_ERR_ORDER = -4,      /* interpolation order other than 3 */
   MLS6_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error) */
   MLS6_ERR_NOMEM = -6,      /* device allocation failed */
-  MLS6_ERR_TIMEOUT = -7,    /* reserved for bounded device waits */
+  MLS6_ERR_TIMEOUT = -7,    /* a bounded device-side wait ran out (kernel gave up) */
   MLS6_ERR_NONFINITE = -8,  /* a position or coefficient was NaN/Inf */
   MLS6_ERR_SIZE = -9        /* request larger than a fixed capacity */
 } mls6_status;
@@ -110,6 +110,18 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
  * MLS6_ERR_NOMEM / _CUDA for device failures; nothing is leaked. */
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision);
+
+/* As mls6_plan, with a smoothing function of continuity C^n,
+ * n = continuity in 1..4 (mls6_plan uses n = 2, Eq. gamma).  The paper
+ * builds gamma from the electrostatic smoothing functions (Sec. II.A.3) and
+ * compares C^1 .. C^4 (Sec. III.B) but prints only n = 2; with u = rho^12,
+ * rho^-6 = u^(-1/2), and gamma_n is its Taylor polynomial about u = 1 to
+ * order n (n = 2 reproduces Eq. gamma), rho^-6 for rho >= 1.  It changes
+ * g_0 .. g_l, the tables and the self term gamma_n(0)/a^6.  Plans with
+ * n != 2 run the per-atom pair kernel only (pair_split 1..8) and refuse
+ * mls6_eval_lb (MLS6_ERR_ARG).  continuity outside 1..4: MLS6_ERR_ARG. */
+int mls6_plan_smooth(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
+                     int levels, int order, int precision, int continuity);
 
 /* Enqueue subsequent work of the plan on a cudaStream_t (NULL = legacy
  * default stream).  Internally an evaluation runs on two streams owned by
@@ -215,24 +227,30 @@ const char* mls6_stage_name(int i);
  * or a negative status. */
 int mls6_auto_levels(const double box[3], double h);
 
-/* Kernel shapes of a plan.  pair_split: lanes per atom of the local pair
- * kernel -- 1, 2, 4 or 8 (each lane group walks its atom's neighbour cells)
- * or 16, 32 (warp form: two or one atoms per warp share one flattened,
- * row-trimmed candidate stream; refused with MLS6_ERR_ARG when the
+/* Kernel shapes of a plan.  pair_split selects the local pair kernel:
+ * 1, 2, 4 or 8 lanes per atom (each lane group walks its atom's neighbour
+ * cells); 16, 32: warp form (two or one atoms per warp share one flattened,
+ * row-trimmed candidate stream, every candidate evaluated branch-free);
+ * 128, 256, 512: queue form (2, 4 or 8 atoms per warp share that stream,
+ * staged in shared memory; the lanes test 32 candidates at a time and the
+ * pairs inside the cutoff are queued and evaluated 32 at a time on full
+ * warps).  The warp and queue forms are refused with MLS6_ERR_ARG when the
  * neighbour range spans more than two cells per side or the box has fewer
- * than five cells along x); stencil_groups: thread groups of 128 sharing one
+ * than five cells along x.  stencil_groups: thread groups of 128 sharing one
  * 8^3 stencil tile (1, 2 or 4; ignored when the stencil tile does not fit in
- * shared memory); 0 keeps the current value.  The defaults come from the
- * plan's size and precision (FP32 / mixed: about 48 resident warps per SM;
- * FP64: the warp form with one atom per warp where allowed; stencil: 24
- * warps per SM).  A shape changes the order of floating-point sums (results
- * move at rounding level), never what is summed.  Waits for the plan's
- * streams; the next evaluation re-captures its graph. */
+ * shared memory); 0 keeps the current value.  Defaults: FP64 the queue form
+ * with two atoms per warp where allowed; otherwise the lanes per atom that
+ * give about 48 resident warps per SM; stencil: 24 warps per SM.  A shape
+ * changes the order of floating-point sums (results move at rounding level),
+ * never what is summed.  Waits for the plan's streams; the next evaluation
+ * re-captures its graph. */
 int mls6_set_tuning(mls6_plan_t* p, int pair_split, int stencil_groups);
 
 /* Which level-stencil kernel the plan runs: 0 shared-memory tiles on the
  * CUDA cores (FP64 / FP32), 1 global-memory fallback (tile and taps beyond
- * the shared-memory budget), 2 tensor cores (MLS6_MIXED), -1 none (l = 1). */
+ * the shared-memory budget), 2 tensor cores through mma.sync (MLS6_MIXED,
+ * not chosen while 3 applies), 3 tensor cores through tcgen05 with the
+ * accumulators in tensor memory (MLS6_MIXED, 2a/h_1 < 9), -1 none (l = 1). */
 int mls6_stencil_kind(const mls6_plan_t* p);
 int mls6_get_tuning(const mls6_plan_t* p, int* pair_split, int* stencil_groups);
 

@@ -52,17 +52,44 @@ int orc_get_threads(void) {
 /* Closed forms.                                                       */
 /* ------------------------------------------------------------------ */
 
-/* Eq. (gamma): 15/8 - 5/4 rho^12 + 3/8 rho^24 below 1, rho^-6 above. */
+/* Smoothing functions of continuity C^n (Sec. II.A.3).  The paper builds
+ * its gamma from the electrostatic smoothing functions: with u = rho^12,
+ * rho^-6 = u^(-1/2), and gamma_n is the Taylor polynomial of u^(-1/2) about
+ * u = 1 to order n,
+ *     gamma_n(rho) = sum_{k=0..n} binom(-1/2, k) (rho^12 - 1)^k   (rho < 1),
+ * which matches rho^-6 and its first n derivatives at rho = 1.  n = 2 is
+ * Eq. (gamma): 15/8 - 5/4 rho^12 + 3/8 rho^24.  The other n (Sec. III.B
+ * compares C^1 .. C^4) follow the same construction, a reading of the
+ * paper, which prints only n = 2. */
+static int g_smooth = 2;
+
+void orc_set_smoothing(int n) { g_smooth = (n >= 1 && n <= 4) ? n : 2; }
+int orc_get_smoothing(void) { return g_smooth; }
+
 double orc_gamma(double rho) {
   if (rho < 1.0) {
-    double r12 = pow(rho, 12.0);
-    return 15.0 / 8.0 - 5.0 / 4.0 * r12 + 3.0 / 8.0 * r12 * r12;
+    double v = pow(rho, 12.0) - 1.0, b = 1.0, term = 1.0, s = 1.0;
+    for (int k = 1; k <= g_smooth; ++k) {
+      b *= (-0.5 - (k - 1)) / k; /* binom(-1/2, k) */
+      term *= v;
+      s += b * term;
+    }
+    return s;
   }
   return pow(rho, -6.0);
 }
 
 double orc_dgamma(double rho) {
-  if (rho < 1.0) return -15.0 * pow(rho, 11.0) + 9.0 * pow(rho, 23.0);
+  if (rho < 1.0) {
+    /* d/drho = 12 rho^11 sum_k k binom(-1/2, k) (rho^12 - 1)^(k-1) */
+    double v = pow(rho, 12.0) - 1.0, b = 1.0, term = 1.0, s = 0.0;
+    for (int k = 1; k <= g_smooth; ++k) {
+      b *= (-0.5 - (k - 1)) / k;
+      s += k * b * term;
+      term *= v;
+    }
+    return 12.0 * pow(rho, 11.0) * s;
+  }
   return -6.0 * pow(rho, -7.0);
 }
 

@@ -29,8 +29,14 @@
 extern "C" {
 #endif
 
+/* Continuity n (1..4) of the smoothing function gamma used by every entry
+ * point below (default 2, Eq. gamma): gamma_n is the order-n Taylor
+ * polynomial of u^(-1/2) about u = 1, u = rho^12.  Process-wide setting. */
+void orc_set_smoothing(int n);
+int  orc_get_smoothing(void);
+
 /* Closed forms (Sec. II.A.3-5). */
-double orc_gamma(double rho);                 /* Eq. (gamma) */
+double orc_gamma(double rho);                 /* Eq. (gamma), C^n variant */
 double orc_dgamma(double rho);                /* d gamma / d rho */
 double orc_gk(int k, int l, double a, double r);   /* Eqs. (g_0), (g_k), (g_l) */
 double orc_dgk(int k, int l, double a, double r);  /* d g_k / dr */

@@ -68,6 +68,10 @@ def lib():
         L.orc_top_table.argtypes = [_dp, C.c_double, _ip, C.c_int, C.c_double, _dp, _dp]
         L.orc_brute.restype = C.c_int
         L.orc_brute.argtypes = [_dp, C.c_double, C.c_int64, _dp, _dp, _dp, _dp, _dp]
+        L.orc_set_smoothing.restype = None
+        L.orc_set_smoothing.argtypes = [C.c_int]
+        L.orc_get_smoothing.restype = C.c_int
+        L.orc_get_smoothing.argtypes = []
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
@@ -93,6 +97,30 @@ def _atoms(x, c):
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
     assert x.shape[0] == c.shape[0]
     return x, c
+
+
+def set_smoothing(n: int) -> None:
+    """Continuity C^n (1..4) of the smoothing function gamma (2 = Eq. gamma)."""
+    lib().orc_set_smoothing(int(n))
+
+
+def smoothing() -> int:
+    return int(lib().orc_get_smoothing())
+
+
+class smoothing_order:
+    """Context manager: evaluate with the C^n smoothing function."""
+
+    def __init__(self, n):
+        self.n = n
+
+    def __enter__(self):
+        self.old = smoothing()
+        set_smoothing(self.n)
+        return self
+
+    def __exit__(self, *exc):
+        set_smoothing(self.old)
 
 
 def set_threads(n: int) -> None:

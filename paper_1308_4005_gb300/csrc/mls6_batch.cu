@@ -247,7 +247,7 @@ static int eval(Batch* b, const void* pos, const void* c, void* forces, double* 
     }
     const int* fl = reinterpret_cast<const int*>(b->h_ew + 7 * B);
     for (size_t r = 0; r < B; ++r)
-      if (fl[r]) return MLS6_ERR_NONFINITE;
+      if (fl[r]) return flag_status(fl[r]);
   }
   return MLS6_OK;
 }

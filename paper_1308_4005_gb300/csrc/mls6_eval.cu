@@ -43,6 +43,10 @@ int launch_reduce(Plan* p, bool vir, cudaStream_t st) {
   return 1;
 }
 
+// Status of the device flag word: bit 1 a bounded wait ran out, bit 0 a
+// non-finite input.
+int flag_status(int f) { return (f & 2) ? MLS6_ERR_TIMEOUT : (f ? MLS6_ERR_NONFINITE : MLS6_OK); }
+
 static bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -91,7 +95,15 @@ template <typename T> static int upload_tables_t(Plan* p) {
   }
   rc = prepare_grid_kernels<T>(p);  // may switch to the global-memory stencil
   if (rc) return rc;
-  if (stencil_tc_eligible(p)) {  // mixed precision: tensor-core stencil tiles
+  rc = prepare_pair_kernels<T>(p);
+  if (rc) return rc;
+  if (stencil_mma_eligible(p)) {  // mixed precision: tcgen05 stencil tiles
+    stencil_mma_geometry(p);
+    p->stencil_mma = true;
+    p->stencil_global = false;
+    rc = prepare_stencil_mma(p);
+    if (rc) return rc;
+  } else if (stencil_tc_eligible(p)) {  // mixed precision: mma.sync stencil tiles
     tc_geometry(p);
     p->stencil_tc = true;
     p->stencil_global = false;
@@ -312,7 +324,7 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
     if (energy && !energy_dev) *energy = p->h_out[0];
     if (virial && !virial_dev)
       for (int c = 0; c < 6; ++c) virial[c] = p->h_out[1 + c];
-    if (*reinterpret_cast<int*>(p->h_out + 7)) return MLS6_ERR_NONFINITE;
+    if (const int f = *reinterpret_cast<int*>(p->h_out + 7)) return flag_status(f);
   }
   return MLS6_OK;
 }
@@ -376,13 +388,14 @@ static int eval_lb_t(Plan* p, const T* pos, const T* sigma, const T* eps, T* for
   if (host) {
     CK(cudaStreamSynchronize(st));
     *energy = p->h_out[0];
-    if (*reinterpret_cast<int*>(p->h_out + 7)) return MLS6_ERR_NONFINITE;
+    if (const int f = *reinterpret_cast<int*>(p->h_out + 7)) return flag_status(f);
   }
   return MLS6_OK;
 }
 
 int eval_lb(Plan* p, const void* pos, const void* sigma, const void* eps, void* forces,
             double* energy) {
+  if (p->sm.n != 2) return MLS6_ERR_ARG;  // Lorentz-Berthelot: Eq. (gamma) only
   if (p->prec == MLS6_FP64)
     return eval_lb_t<double>(p, (const double*)pos, (const double*)sigma, (const double*)eps,
                              (double*)forces, energy);

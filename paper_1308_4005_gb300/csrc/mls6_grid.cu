@@ -575,6 +575,7 @@ bool stencil_fuses_top(const Plan* p) { return p->levels >= 2 && !p->stencil_glo
 
 template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
   if (p->levels < 2) return 0;
+  if (p->stencil_mma) return launch_stencil_mma(p, vir, stencil_fuses_top(p), st);
   if (p->stencil_tc) return launch_stencil_tc(p, vir, stencil_fuses_top(p), st);
   StencilArgs<T> A = stencil_args<T>(p);
   double* wp = p->d_wpart + 6 * p->wpart_stencil;

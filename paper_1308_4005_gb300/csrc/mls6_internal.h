@@ -27,7 +27,7 @@ constexpr int kStencilThreads = 128;
 constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
 constexpr size_t kStencilSmemMax = 200 * 1024;  // dynamic shared memory of a stencil tile
 constexpr double kCellDiv = 2.0;  // cell width >= a / kCellDiv
-constexpr int kPairSplitMax = 32;  // lanes per atom of the pair kernel: 1 .. 32
+constexpr int kPairSplitMax = 32;  // pair-kernel blocks are at most N * kPairSplitMax / kBlock
 
 // 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
@@ -43,6 +43,13 @@ struct CellGeom {
   double w[3];      // cell width
   double inv_w[3];
   long ncell;
+};
+
+// Smoothing function gamma of continuity C^n: gamma = sum_k c[k] u^k for
+// rho < 1, u = rho^12 (n = 2: Eq. gamma).
+struct Smooth {
+  int n = 2;
+  double c[5] = {1.875, -1.25, 0.375, 0.0, 0.0};
 };
 
 // One grid level.
@@ -63,6 +70,7 @@ struct Plan {
 
   CellGeom cg;
   Level lv[kMaxLevels + 1];  // 1-based
+  Smooth sm;                 // smoothing function
   double c_self;             // gamma(0)/a^6
 
   // Level-1 stencil: taps m with |m h_1| < 2a, shared by all levels k < l
@@ -80,8 +88,13 @@ struct Plan {
   size_t stencil_smem = 0;
   bool stencil_global = false;  // tile does not fit in shared memory
   int stencil_groups = 1;       // thread groups (of 128) sharing one tile
-  bool stencil_tc = false;      // tensor-core stencil (mixed precision)
+  bool stencil_tc = false;      // mma.sync tensor-core stencil (mixed precision)
   uint32_t* d_tcw = nullptr;    // its packed split weight pairs
+  bool stencil_mma = false;     // tcgen05 tensor-core stencil (mixed precision)
+  int mma_rows_pad_v = 0, mma_rows_pad_e = 0;  // tap rows padded to whole chunks
+  int* d_mma_rows = nullptr;    // padded row table (int4: dy, dz, R, first)
+  uint8_t* d_mma_bv = nullptr;  // B matrices, energy + six virial channels
+  uint8_t* d_mma_be = nullptr;  // B matrices, energy channel only
   // coarsest level tables
   std::vector<double> h_top_T, h_top_V;
 
@@ -114,7 +127,7 @@ struct Plan {
   // current split are written and summed)
   long wpart_stencil = 0, wpart_top = 0, wpart_pair = 0;
   double* d_out = nullptr;     // [0] energy, [1..6] virial; [8..] kReduceGroups slice sums of 6
-  int* d_flag = nullptr;       // [0] non-finite, [1] interpolation ticket, [2] tile-pass ticket,
+  int* d_flag = nullptr;       // [0] bit 0 non-finite, bit 1 wait timeout, [1] interpolation ticket, [2] tile-pass ticket,
                                // [3] max cell population, [4..5] max |c| (double),
                                // [6..7] max sqrt(2 eps) (double, Lorentz-Berthelot)
   double* h_out = nullptr;     // pinned host staging of d_out
@@ -145,10 +158,11 @@ struct Plan {
 };
 
 // host helpers (mls6_plan.cpp)
-double gamma_fn(double rho);
-double dgamma_over_rho(double rho);  // gamma'(rho)/rho
-double g_level(int k, int l, double a, double r);
-double dg_level_over_r(int k, int l, double a, double r);
+Smooth smooth_coefficients(int continuity);
+double gamma_fn(const Smooth& s, double rho);
+double dgamma_over_rho(const Smooth& s, double rho);  // gamma'(rho)/rho
+double g_level(const Smooth& s, int k, int l, double a, double r);
+double dg_level_over_r(const Smooth& s, int k, int l, double a, double r);
 
 // launch sequence (mls6_eval.cu)
 int eval_launch(Plan* p, const void* pos, const void* c, void* forces, double* energy,
@@ -176,13 +190,14 @@ template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st);
 template <typename T>
 int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_t st);
 template <typename T> int prepare_grid_kernels(Plan* p);
+template <typename T> int prepare_pair_kernels(Plan* p);
 int launch_reduce(Plan* p, bool vir, cudaStream_t st);
+int flag_status(int flag_word);  // mls6_eval.cu
 int pair_split(const Plan* p);  // default lanes per atom of the pair kernel (mls6_pair.cu)
 bool pair_cluster_ok(const Plan* p);  // warp form usable (mls6_pair.cu)
 // virial partial records summed by the final reduction
-inline long wpart_used(const Plan* p) {
-  return p->wpart_pair + (p->N > 0 ? (p->N * p->pair_split + kBlock - 1) / kBlock : 0);
-}
+long pair_blocks(const Plan* p, int split);  // blocks of the pair kernel (mls6_pair.cu)
+inline long wpart_used(const Plan* p) { return p->wpart_pair + pair_blocks(p, p->pair_split); }
 bool stencil_fuses_top(const Plan* p);
 // tensor-core stencil (mls6_stencil_tc.cu)
 size_t tc_smem_bytes(int P);
@@ -191,5 +206,10 @@ void tc_geometry(Plan* p);
 std::vector<uint32_t> tc_weight_table(const Plan* p);
 int prepare_stencil_tc(Plan* p);
 int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st);
+// tcgen05 stencil (mls6_stencil_mma.cu)
+bool stencil_mma_eligible(const Plan* p);
+void stencil_mma_geometry(Plan* p);
+int prepare_stencil_mma(Plan* p);
+int launch_stencil_mma(Plan* p, bool vir, bool fuse_top, cudaStream_t st);
 
 }  // namespace mls6

@@ -19,7 +19,31 @@ template <typename T> struct PairArgs {
   int nc[3], R[3];
   T a2, ia2, ia6, ia8;
   T margin;  // absolute slack of the row trimming (covers rounding of x, x/w)
+  T Lhi[3], Llo[3];  // box length as an unevaluated sum hi + lo (exact image shifts)
+  // smoothing function of continuity other than C^2 (GEN kernels):
+  // gamma = sum gc[k] u^k, u = rho^12; gamma'(rho)/rho = -12 rho^10 ... as
+  // g_0'/r = -6 r^-8 + a^-8 rho^10 sum gd[k] u^k with gd[k] = -12 (k+1) gc[k+1]
+  T gc[5], gd[4];
 };
+
+// Eq. (g_0) and g_0'(r)/r from inv = 1/r^2, s1 = (r/a)^2: the C^2 smoothing
+// function of Eq. (gamma) with its coefficients inline, or (GEN) the
+// coefficients of the plan's smoothing function.
+template <typename T, bool GEN>
+__device__ __forceinline__ void g0_and_gp(T inv, T s1, const PairArgs<T>& g, T& g0, T& gp) {
+  const T inv3 = inv * inv * inv;
+  const T s2 = s1 * s1, s3 = s2 * s1, s6 = s3 * s3;
+  const T s5 = s3 * s2;
+  if (GEN) {
+    const T P = g.gc[0] + s6 * (g.gc[1] + s6 * (g.gc[2] + s6 * (g.gc[3] + s6 * g.gc[4])));
+    const T D = g.gd[0] + s6 * (g.gd[1] + s6 * (g.gd[2] + s6 * g.gd[3]));
+    g0 = inv3 - g.ia6 * P;
+    gp = T(-6) * inv3 * inv + g.ia8 * s5 * D;
+  } else {
+    g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
+    gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
+  }
+}
 
 // i = m n + iw with 0 <= iw < n: the cell iw and periodic image m of an
 // unwrapped cell index (|m| is 0 or 1 unless the box is thinner than the
@@ -55,7 +79,7 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdiv
 // sigma_i in place of c_i and lbw holds sqrt(2 eps_i) in sorted order; the
 // pair coefficient is C_ij = lbw_i lbw_j ((sigma_i + sigma_j)/2)^6, and the
 // outputs are e0_i = sum_j C_ij g_0 and F_i = -sum_j C_ij g_0'/r d.
-template <typename T, bool VIR, int S, bool LB = false>
+template <typename T, bool VIR, int S, bool LB = false, bool GEN = false>
 __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
                                                   PairArgs<T> g, T* __restrict__ e0,
@@ -113,12 +137,8 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
             const bool valid = (j + u < j1) && !(same && j + u == i);
             if (valid && r2 < g.a2) {
-              const T inv = rcp(r2);
-              const T inv3 = inv * inv * inv;
-              const T s = r2 * g.ia2, s2 = s * s, s3 = s2 * s, s6 = s3 * s3;
-              const T s5 = s3 * s2;
-              const T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
-              const T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
+              T g0, gp;
+              g0_and_gp<T, GEN>(rcp(r2), r2 * g.ia2, g, g0, gp);
               T cj = pj[u].w;
               if (LB) {
                 const T sg = T(0.5) * (ci + pj[u].w), sg3 = sg * sg * sg;
@@ -397,19 +417,351 @@ __global__ void __launch_bounds__(kBlock) k_pair_warp(const Vec4<T>* __restrict_
   }
 }
 
+
+// One queued pair of the queue form: displacement with an exact image shift,
+// then Eq. (g_0) and its derivative accumulated into the lane's sums.
+// en = {j, image code (mx+8) | (my+8) << 4 | (mz+8) << 8}: the neighbour is
+// x_j + m L.  The box length is the unevaluated sum Lhi + Llo, and the
+// shift is applied to whichever of x_i, x_j lies near the far face
+// (x_i - Lhi for m = +1, x_j - Lhi for m = -1), where the subtraction is
+// exact: an image pair carries no rounding of the box length or of the
+// absolute coordinates.
+template <typename T, bool VIR, bool LB>
+__device__ __forceinline__ void pair_eval(int2 en, const Vec4<T>* __restrict__ sp,
+                                          const T* __restrict__ lbw, const Vec4<T>& pi, T wi,
+                                          const PairArgs<T>& g, T& e, T& fx, T& fy, T& fz, T& w0,
+                                          T& w1, T& w2, T& w3, T& w4, T& w5) {
+  constexpr int kImg0 = 8 | (8 << 4) | (8 << 8);
+  const Vec4<T> pj = sp[en.x];
+  T ddx = pj.x - pi.x, ddy = pj.y - pi.y, ddz = pj.z - pi.z;
+  if (en.y != kImg0) {
+    const int m[3] = {(en.y & 15) - 8, ((en.y >> 4) & 15) - 8, ((en.y >> 8) & 15) - 8};
+    const T xj[3] = {pj.x, pj.y, pj.z}, xi[3] = {pi.x, pi.y, pi.z};
+    T d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T sh = (T)m[a] * g.Lhi[a];
+      const T sj = m[a] < 0 ? xj[a] + sh : xj[a];
+      const T si = m[a] > 0 ? xi[a] - sh : xi[a];
+      d[a] = (sj - si) + (T)m[a] * g.Llo[a];
+    }
+    ddx = d[0];
+    ddy = d[1];
+    ddz = d[2];
+  }
+  const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  const T inv = rcp(r2);
+  const T inv3 = inv * inv * inv;
+  const T s1 = r2 * g.ia2, s2 = s1 * s1, s3 = s2 * s1, s6 = s3 * s3;
+  const T s5 = s3 * s2;
+  const T g0 = inv3 - g.ia6 * (T(1.875) - T(1.25) * s6 + T(0.375) * s6 * s6);
+  const T gp = T(-6) * inv3 * inv + g.ia8 * s5 * (T(15) - T(9) * s6);
+  T cj = pj.w;
+  if (LB) {
+    const T sg = T(0.5) * (pi.w + pj.w), sg3 = sg * sg * sg;
+    cj = wi * lbw[en.x] * sg3 * sg3;
+  }
+  e += cj * g0;
+  const T cg = cj * gp;
+  fx += cg * ddx;
+  fy += cg * ddy;
+  fz += cg * ddz;
+  if (VIR) {  // virial records carry c_i (the lanes mix atoms)
+    const T cv = LB ? cg : pi.w * cg;
+    const T cx_ = cv * ddx, cy_ = cv * ddy;
+    w0 += cx_ * ddx;
+    w1 += cy_ * ddy;
+    w2 += cv * ddz * ddz;
+    w3 += cx_ * ddy;
+    w4 += cx_ * ddz;
+    w5 += cy_ * ddz;
+  }
+}
+
+// Stage candidates c0 .. c0+cn-1 of a warp's stream in shared memory: the
+// position shifted by its piece's periodic image (for the cutoff test) and
+// {j, image code} (for the evaluation).
+template <typename T>
+__device__ __forceinline__ void q_stage(int c0, int cn, int lane, const int* t_end,
+                                        const int* t_base, const int* t_img,
+                                        const Vec4<T>* __restrict__ sp, const PairArgs<T>& g,
+                                        Vec4<T>* cpos, int2* cidx) {
+  constexpr int kImg0 = 8 | (8 << 4) | (8 << 8);
+  int p = -1, pend = 0, pbase = 0, pimg = kImg0;
+  T sx = 0, sy = 0, sz = 0;
+  for (int u = lane; u < cn; u += 32) {
+    const int k = c0 + u;
+    if (k >= pend) {
+      do {
+        ++p;
+        pend = t_end[p];
+      } while (k >= pend);
+      pbase = t_base[p];
+      pimg = t_img[p];
+      sx = (T)((pimg & 15) - 8) * g.box.L[0];
+      sy = (T)(((pimg >> 4) & 15) - 8) * g.box.L[1];
+      sz = (T)(((pimg >> 8) & 15) - 8) * g.box.L[2];
+    }
+    const int j = pbase + k;
+    Vec4<T> pj = sp[j];
+    pj.x += sx;
+    pj.y += sy;
+    pj.z += sz;
+    cpos[u] = pj;
+    cidx[u] = make_int2(j, pimg);
+  }
+}
+
+// Queue form of the pair sum (pair_split 64 G: G = 2, 4 or 8 atoms per
+// warp, kQWarps warps per block).  The G consecutive sorted atoms of a warp
+// that share a row of cells form a segment, and the segment's candidate
+// stream is built as in the warp form (lane t: neighbour row t trimmed
+// against the segment's bounding box, a warp scan flattening the pieces).
+// The stream is staged in shared memory (positions shifted by their
+// periodic image, chunks of qcap<T>() candidates), so the G atoms read the
+// candidates from global memory once.  Each atom then tests the staged
+// candidates 32 at a time (0 < r^2 < a^2: the atom itself is the only
+// candidate at distance 0), the hits of the 32 lanes are compacted by a
+// ballot into a per-warp queue, and whenever 32 hits are queued all 32
+// lanes evaluate one each.  The pair arithmetic therefore runs on full warps
+// and only on pairs inside the cutoff.  The queue is filled and drained in
+// stream order and each lane sums its evaluations in that order, then a
+// fixed shuffle tree combines the lanes: results are reproducible bit for
+// bit.
+constexpr int kQWarps = 4;
+template <typename T> __host__ __device__ constexpr int qcap() {
+  return sizeof(T) == 4 ? 512 : 256;
+}
+template <typename T> constexpr size_t q_smem_bytes() {
+  return (size_t)kQWarps * qcap<T>() * (sizeof(Vec4<T>) + sizeof(int2));
+}
+
+template <typename T, bool VIR, int G, bool LB = false>
+__global__ void __launch_bounds__(kQWarps * 32) k_pair_q(const Vec4<T>* __restrict__ sp,
+                                                          const int* __restrict__ start, int N,
+                                                          PairArgs<T> g, T* __restrict__ e0,
+                                                          T* __restrict__ floc,
+                                                          double* __restrict__ wpart,
+                                                          const T* __restrict__ lbw = nullptr) {
+  constexpr int kW = kQWarps;
+  constexpr int kP = 3 * 32;   // pieces of one segment: <= 3 per row, <= 32 rows
+  constexpr int kQ = 64;       // queued hits: < 32 left over + 32 new
+  constexpr int kCap = qcap<T>();
+  constexpr unsigned kAll = 0xffffffffu;
+  __shared__ double sh[32 * 6];
+  __shared__ int t_end[kW][kP], t_base[kW][kP], t_img[kW][kP];
+  __shared__ int2 qu[kW][kQ];
+  extern __shared__ __align__(16) unsigned char q_dyn[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Vec4<T>* cpos = reinterpret_cast<Vec4<T>*>(q_dyn) + (size_t)wid * kCap;
+  int2* cidx = reinterpret_cast<int2*>(q_dyn + (size_t)kW * kCap * sizeof(Vec4<T>)) +
+               (size_t)wid * kCap;
+  const long i0 = ((long)blockIdx.x * kW + wid) * G;
+  const int nat = (int)max(0L, min((long)G, (long)N - i0));  // atoms of this warp
+  // lane t < nat holds atom i0 + t
+  Vec4<T> pa = {T(0), T(0), T(0), T(0)};
+  int cx = 0, cy = 0, cz = 0, rid = INT_MAX;
+  if (lane < nat) {
+    pa = sp[i0 + lane];
+    cx = min(max((int)(pa.x * g.inv_w[0]), 0), g.nc[0] - 1);
+    cy = min(max((int)(pa.y * g.inv_w[1]), 0), g.nc[1] - 1);
+    cz = min(max((int)(pa.z * g.inv_w[2]), 0), g.nc[2] - 1);
+    rid = cy + g.nc[1] * cz;
+  }
+  T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+  const int ny = 2 * g.R[1] + 1, nrows = (2 * g.R[2] + 1) * ny;
+  for (int s = 0; s < nat;) {
+    const int rs = __shfl_sync(kAll, rid, s);
+    const unsigned seg = __ballot_sync(kAll, lane < nat && rid == rs);
+    const bool act = (seg >> lane) & 1u;
+    // bounding box of the segment
+    T xmn = act ? pa.x : T(INFINITY), xmx = act ? pa.x : T(-INFINITY);
+    T ymn = act ? pa.y : T(INFINITY), ymx = act ? pa.y : T(-INFINITY);
+    T zmn = act ? pa.z : T(INFINITY), zmx = act ? pa.z : T(-INFINITY);
+    int cxmn = act ? cx : INT_MAX, cxmx = act ? cx : INT_MIN;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {  // over the lanes 0..G-1 that hold atoms
+      xmn = min(xmn, __shfl_xor_sync(kAll, xmn, o));
+      xmx = max(xmx, __shfl_xor_sync(kAll, xmx, o));
+      ymn = min(ymn, __shfl_xor_sync(kAll, ymn, o));
+      ymx = max(ymx, __shfl_xor_sync(kAll, ymx, o));
+      zmn = min(zmn, __shfl_xor_sync(kAll, zmn, o));
+      zmx = max(zmx, __shfl_xor_sync(kAll, zmx, o));
+      cxmn = min(cxmn, __shfl_xor_sync(kAll, cxmn, o));
+      cxmx = max(cxmx, __shfl_xor_sync(kAll, cxmx, o));
+    }
+    // every lane sets up a row: broadcast the box from lane 0
+    xmn = __shfl_sync(kAll, xmn, 0);
+    xmx = __shfl_sync(kAll, xmx, 0);
+    ymn = __shfl_sync(kAll, ymn, 0);
+    ymx = __shfl_sync(kAll, ymx, 0);
+    zmn = __shfl_sync(kAll, zmn, 0);
+    zmx = __shfl_sync(kAll, zmx, 0);
+    cxmn = __shfl_sync(kAll, cxmn, 0);
+    cxmx = __shfl_sync(kAll, cxmx, 0);
+    const int scy = __shfl_sync(kAll, cy, s), scz = __shfl_sync(kAll, cz, s);
+    // 1. lane t: row t of the (2R+1)^2 neighbour rows, trimmed and split
+    //    into at most three same-image pieces
+    int np = 0, cnt = 0;
+    int pj0[3] = {0, 0, 0}, pn[3] = {0, 0, 0}, pim[3] = {0, 0, 0};
+    if (lane < nrows) {
+      const int dz = lane / ny - g.R[2], dy = lane % ny - g.R[1];
+      const int z = scz + dz, y = scy + dy;
+      int iz, iy, mz, my;
+      wrap_image(z, g.nc[2], iz, mz);
+      wrap_image(y, g.nc[1], iy, my);
+      const T ylo = (T)y * g.w[1], zlo = (T)z * g.w[2];
+      const T dyl = max(T(0), max(ylo - ymx, ymn - (ylo + g.w[1])) - g.margin);
+      const T dzl = max(T(0), max(zlo - zmx, zmn - (zlo + g.w[2])) - g.margin);
+      const T d2 = dyl * dyl + dzl * dzl;
+      if (d2 < g.a2) {
+        const T rx = sqrt(g.a2 - d2) + g.margin;
+        const int xl = max(cxmn - g.R[0], (int)floor((xmn - rx) * g.inv_w[0]));
+        const int xh = min(cxmx + g.R[0], (int)floor((xmx + rx) * g.inv_w[0]));
+        const int row = g.nc[0] * (iy + g.nc[1] * iz);
+        const int img_yz = ((my + 8) << 4) | ((mz + 8) << 8);
+        int xa = xl, ix, mx;
+        wrap_image(xl, g.nc[0], ix, mx);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (xa <= xh) {
+            const int xb = min(xh, xa + (g.nc[0] - 1 - ix));
+            pj0[q] = start[row + ix];
+            pn[q] = start[row + ix + (xb - xa) + 1] - pj0[q];
+            pim[q] = img_yz | (mx + 8);
+            cnt += pn[q];
+            np = q + 1;
+            xa = xb + 1;
+            ix = 0;
+            ++mx;
+          }
+        }
+      }
+    }
+    // 2. pieces -> one stream
+    int np_inc = np, c_inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kAll, np_inc, o), b = __shfl_up_sync(kAll, c_inc, o);
+      if (lane >= o) {
+        np_inc += a;
+        c_inc += b;
+      }
+    }
+    const int total = __shfl_sync(kAll, c_inc, 31);
+    {
+      int slot = np_inc - np, cend = c_inc - cnt;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < np) {
+          cend += pn[q];
+          t_end[wid][slot] = cend;
+          t_base[wid][slot] = pj0[q] - (cend - pn[q]);
+          t_img[wid][slot] = pim[q];
+          ++slot;
+        }
+    }
+    __syncwarp();
+    const bool one = total <= kCap;
+    if (one) q_stage<T>(0, total, lane, t_end[wid], t_base[wid], t_img[wid], sp, g, cpos, cidx);
+    __syncwarp();
+    // 3. every atom of the segment against the stream
+    const int send = s + __popc(seg);
+    for (; s < send; ++s) {
+      const int i = (int)(i0 + s);
+      Vec4<T> pi;
+      pi.x = __shfl_sync(kAll, pa.x, s);
+      pi.y = __shfl_sync(kAll, pa.y, s);
+      pi.z = __shfl_sync(kAll, pa.z, s);
+      pi.w = __shfl_sync(kAll, pa.w, s);
+      T wi = T(0);
+      if (LB) wi = lbw[i];
+      T e = 0, fx = 0, fy = 0, fz = 0;
+      int qn = 0;
+      for (int c0 = 0; c0 < total; c0 += kCap) {
+        const int cn = min(kCap, total - c0);
+        if (!one) {
+          __syncwarp();
+          q_stage<T>(c0, cn, lane, t_end[wid], t_base[wid], t_img[wid], sp, g, cpos, cidx);
+          __syncwarp();
+        }
+        for (int u0 = 0; u0 < cn; u0 += 32) {
+          const int u = u0 + lane;
+          bool hit = false;
+          if (u < cn) {
+            const Vec4<T> pj = cpos[u];
+            const T ddx = pj.x - pi.x, ddy = pj.y - pi.y, ddz = pj.z - pi.z;
+            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            hit = r2 < g.a2 && r2 > T(0);
+          }
+          const unsigned m = __ballot_sync(kAll, hit);
+          if (hit) qu[wid][qn + __popc(m & ((1u << lane) - 1u))] = cidx[u];
+          qn += __popc(m);
+          if (qn >= 32) {
+            __syncwarp();
+            pair_eval<T, VIR, LB>(qu[wid][lane], sp, lbw, pi, wi, g, e, fx, fy, fz, w0, w1, w2,
+                                  w3, w4, w5);
+            __syncwarp();
+            if (lane < qn - 32) qu[wid][lane] = qu[wid][lane + 32];
+            __syncwarp();
+            qn -= 32;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane < qn)
+        pair_eval<T, VIR, LB>(qu[wid][lane], sp, lbw, pi, wi, g, e, fx, fy, fz, w0, w1, w2, w3,
+                              w4, w5);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(kAll, e, o);
+        fx += __shfl_xor_sync(kAll, fx, o);
+        fy += __shfl_xor_sync(kAll, fy, o);
+        fz += __shfl_xor_sync(kAll, fz, o);
+      }
+      if (lane == 0) {
+        const T cf = LB ? T(1) : pi.w;
+        e0[i] = e;
+        floc[3 * (size_t)i + 0] = -cf * fx;
+        floc[3 * (size_t)i + 1] = -cf * fy;
+        floc[3 * (size_t)i + 2] = -cf * fz;
+      }
+      __syncwarp();  // the queue is reused by the next atom
+    }
+    __syncwarp();  // the next segment rewrites the piece table and the stage
+  }
+  if (VIR) {
+    T wv[6] = {w0, w1, w2, w3, w4, w5};
+    double ws[6];
+    block_sum_lo<T, 6>(wv, ws, sh);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * ws[c];
+  }
+}
+
 bool pair_cluster_ok(const Plan* p) {
+  if (p->sm.n != 2) return false;  // warp and queue forms: Eq. (gamma) only
   for (int d = 0; d < 3; ++d)
     if (p->cg.R[d] > 2) return false;
   return p->cg.nc[0] >= 2 * p->cg.R[0] + 1;
 }
 
-// Lanes per atom.  FP32 and mixed: the smallest of 1, 2, 4, 8 that gives
-// about 48 resident warps per SM on a 152-SM GPU (the per-atom kernel wins
-// where the hit arithmetic is cheap).  FP64: the warp form with one atom
-// per warp where it applies (its branch-free pair arithmetic keeps all
-// lanes busy on the slow FP64 pipe: 1.86 vs 2.22 ms on a 65,536-atom slab).
+long pair_blocks(const Plan* p, int split) {
+  const long N = p->N;
+  if (N <= 0) return 0;
+  if (split >= 64) return cdiv(cdiv(N, split / 64), kQWarps);
+  return cdiv(N * split, kBlock);
+}
+
+// Default pair kernel: FP64 the queue form where the cell geometry allows
+// it; otherwise the smallest of 1, 2, 4, 8 lanes per atom that gives about
+// 48 resident warps per SM on a 152-SM GPU.
 int pair_split(const Plan* p) {
-  if (p->prec == MLS6_FP64 && pair_cluster_ok(p)) return 32;
+  // FP64: the queue form with two atoms per warp where the cell geometry
+  // allows it (1M-atom cube 24.5 ms against 29.4 ms per atom and 31.2 ms
+  // for the warp form); FP32 keeps the per-atom kernel (868 us there against
+  // 2.25 ms for the best queue form)
+  if (p->prec == MLS6_FP64 && pair_cluster_ok(p)) return 128;
   const long want = 152L * 48 * 32;
   int s = 1;
   while (s < 8 && p->N * s < want) s *= 2;
@@ -420,6 +772,17 @@ template <typename T, int S>
 static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
   const int N = (int)p->N;
   const long nb = cdiv((long)N * S, kBlock);
+  if (p->sm.n != 2 && !lb) {  // smoothing function other than Eq. (gamma)
+    if (vir)
+      k_pair<T, true, S, false, true><<<nb, kBlock, 0, st>>>(
+          (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
+          p->d_wpart + 6 * p->wpart_pair);
+    else
+      k_pair<T, false, S, false, true><<<nb, kBlock, 0, st>>>(
+          (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
+          p->d_wpart + 6 * p->wpart_pair);
+    return;
+  }
   if (lb)
     k_pair<T, false, S, true><<<nb, kBlock, 0, st>>>(
         (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
@@ -452,6 +815,46 @@ static void launch_w(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStre
                                                     (T*)p->d_floc, p->d_wpart + 6 * p->wpart_pair);
 }
 
+template <typename T, int G>
+static void launch_q(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
+  const int N = (int)p->N;
+  const long nb = pair_blocks(p, 64 * G);
+  if (nb == 0) return;
+  const size_t sm = q_smem_bytes<T>();
+  const int th = kQWarps * 32;
+  if (lb)
+    k_pair_q<T, false, G, true><<<nb, th, sm, st>>>(
+        (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
+        p->d_wpart + 6 * p->wpart_pair, (const T*)p->d_lbw);
+  else if (vir)
+    k_pair_q<T, true, G><<<nb, th, sm, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+                                             pg, (T*)p->d_e0, (T*)p->d_floc,
+                                             p->d_wpart + 6 * p->wpart_pair);
+  else
+    k_pair_q<T, false, G><<<nb, th, sm, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+                                              pg, (T*)p->d_e0, (T*)p->d_floc,
+                                              p->d_wpart + 6 * p->wpart_pair);
+}
+
+template <typename T, int G> static int q_attr() {
+  const int sm = (int)q_smem_bytes<T>();
+  const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (cudaFuncSetAttribute(k_pair_q<T, true, G>, a, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pair_q<T, false, G>, a, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pair_q<T, false, G, true>, a, sm) != cudaSuccess)
+    return MLS6_ERR_CUDA;
+  return MLS6_OK;
+}
+
+// Shared-memory limits of the queue-form instantiations (plan creation,
+// outside any stream capture).
+template <typename T> int prepare_pair_kernels(Plan*) {
+  if (q_attr<T, 2>() || q_attr<T, 4>() || q_attr<T, 8>()) return MLS6_ERR_CUDA;
+  return MLS6_OK;
+}
+template int prepare_pair_kernels<float>(Plan*);
+template int prepare_pair_kernels<double>(Plan*);
+
 template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb) {
   PairArgs<T> pg;
   for (int d = 0; d < 3; ++d) {
@@ -471,7 +874,16 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool l
   pg.ia2 = (T)(1.0 / (p->a * p->a));
   pg.ia6 = (T)std::pow(p->a, -6.0);
   pg.ia8 = (T)std::pow(p->a, -8.0);
+  for (int d = 0; d < 3; ++d) {
+    pg.Lhi[d] = (T)p->L[d];
+    pg.Llo[d] = (T)(p->L[d] - (double)pg.Lhi[d]);
+  }
+  for (int k = 0; k < 5; ++k) pg.gc[k] = (T)p->sm.c[k];
+  for (int k = 0; k < 4; ++k) pg.gd[k] = (T)(-12.0 * (k + 1) * p->sm.c[k + 1]);
   switch (p->pair_split) {
+    case 512: launch_q<T, 8>(p, pg, vir, lb, st); break;
+    case 256: launch_q<T, 4>(p, pg, vir, lb, st); break;
+    case 128: launch_q<T, 2>(p, pg, vir, lb, st); break;
     case 32: launch_w<T, 1>(p, pg, vir, lb, st); break;
     case 16: launch_w<T, 2>(p, pg, vir, lb, st); break;
     case 8: launch_s<T, 8>(p, pg, vir, lb, st); break;

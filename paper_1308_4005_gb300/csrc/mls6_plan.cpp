@@ -15,62 +15,88 @@
 
 namespace mls6 {
 
-// Eq. (gamma): 15/8 - 5/4 rho^12 + 3/8 rho^24 for rho < 1, rho^-6 above.
-double gamma_fn(double rho) {
+// Smoothing function of continuity C^n (Sec. II.A.3): with u = rho^12 the
+// kernel rho^-6 is u^(-1/2), and gamma_n is its Taylor polynomial about
+// u = 1 to order n, written out in powers of u, gamma_n = sum_k c_k u^k for
+// rho < 1 and rho^-6 above.  n = 2 is Eq. (gamma): 15/8 - 5/4 rho^12 +
+// 3/8 rho^24; n = 1, 3, 4 are the other continuities of Sec. III.B built
+// the same way.
+Smooth smooth_coefficients(int n) {
+  Smooth s;
+  s.n = n;
+  for (int k = 0; k < 5; ++k) s.c[k] = 0.0;
+  // sum_{j<=n} binom(-1/2, j) (u - 1)^j, expanded: c_k += binom(-1/2, j) binom(j, k) (-1)^(j-k)
+  double bj = 1.0;
+  for (int j = 0; j <= n; ++j) {
+    if (j > 0) bj *= (-0.5 - (j - 1)) / j;
+    double bjk = 1.0;  // binom(j, k)
+    for (int k = 0; k <= j; ++k) {
+      if (k > 0) bjk = bjk * (j - k + 1) / k;
+      s.c[k] += bj * bjk * (((j - k) & 1) ? -1.0 : 1.0);
+    }
+  }
+  return s;
+}
+
+double gamma_fn(const Smooth& s, double rho) {
   if (rho < 1.0) {
-    double r2 = rho * rho, r4 = r2 * r2, r12 = r4 * r4 * r4;
-    return 1.875 - 1.25 * r12 + 0.375 * r12 * r12;
+    double r2 = rho * rho, r4 = r2 * r2, u = r4 * r4 * r4;
+    double v = s.c[s.n];
+    for (int k = s.n - 1; k >= 0; --k) v = v * u + s.c[k];
+    return v;
   }
   double r2 = rho * rho;
   return 1.0 / (r2 * r2 * r2);
 }
 
-// gamma'(rho)/rho = -15 rho^10 + 9 rho^22 (rho < 1), -6 rho^-8 (rho >= 1).
-double dgamma_over_rho(double rho) {
+// gamma'(rho)/rho = 12 rho^10 sum_k k c_k u^(k-1) (rho < 1), -6 rho^-8 (rho >= 1).
+double dgamma_over_rho(const Smooth& s, double rho) {
   double r2 = rho * rho;
   if (rho < 1.0) {
-    double r10 = r2 * r2 * r2 * r2 * r2;
-    return -15.0 * r10 + 9.0 * r10 * r10 * r2;
+    double r4 = r2 * r2, u = r4 * r4 * r4, r10 = r4 * r4 * r2;
+    double v = s.n * s.c[s.n];
+    for (int k = s.n - 1; k >= 1; --k) v = v * u + k * s.c[k];
+    return 12.0 * r10 * v;
   }
   double r8 = r2 * r2 * r2 * r2;
   return -6.0 / r8;
 }
 
-static double sgamma(double s, double r) {  // s^-6 gamma(r/s)
+static double sgamma(const Smooth& sm, double s, double r) {  // s^-6 gamma(r/s)
   double s2 = s * s;
-  return gamma_fn(r / s) / (s2 * s2 * s2);
+  return gamma_fn(sm, r / s) / (s2 * s2 * s2);
 }
 
-static double sdgamma_over_r(double s, double r) {  // (d/dr s^-6 gamma(r/s)) / r
+static double sdgamma_over_r(const Smooth& sm, double s, double r) {  // (d/dr s^-6 gamma(r/s)) / r
   double s2 = s * s;
-  return dgamma_over_rho(r / s) / (s2 * s2 * s2 * s2);
+  return dgamma_over_rho(sm, r / s) / (s2 * s2 * s2 * s2);
 }
 
 // Eqs. (g_0), (g_k), (g_l); exactly 0 beyond the cutoff of levels k < l.
-double g_level(int k, int l, double a, double r) {
+double g_level(const Smooth& sm, int k, int l, double a, double r) {
   if (k == 0) {
     if (r >= a) return 0.0;
     double r2 = r * r;
-    return 1.0 / (r2 * r2 * r2) - sgamma(a, r);
+    return 1.0 / (r2 * r2 * r2) - sgamma(sm, a, r);
   }
   double si = std::ldexp(a, k - 1);
-  if (k == l) return sgamma(si, r);
+  if (k == l) return sgamma(sm, si, r);
   double so = std::ldexp(a, k);
   if (r >= so) return 0.0;
-  return sgamma(si, r) - sgamma(so, r);
+  return sgamma(sm, si, r) - sgamma(sm, so, r);
 }
 
-double dg_level_over_r(int k, int l, double a, double r) {
+double dg_level_over_r(const Smooth& sm, int k, int l, double a, double r) {
   if (k == 0) {
     if (r >= a) return 0.0;
     double r2 = r * r;
-    return -6.0 / (r2 * r2 * r2 * r2) - sdgamma_over_r(a, r);
+    return -6.0 / (r2 * r2 * r2 * r2) - sdgamma_over_r(sm, a, r);
   }
   double si = std::ldexp(a, k - 1);
-  if (k == l) return sdgamma_over_r(si, r);
+  if (k == l) return sdgamma_over_r(sm, si, r);
   double so = std::ldexp(a, k);
   if (r >= so) return 0.0;
-  return sdgamma_over_r(si, r) - sdgamma_over_r(so, r);
+  return sdgamma_over_r(sm, si, r) - sdgamma_over_r(sm, so, r);
 }
 
 // ------------------------------------------------------------------------
@@ -126,8 +152,8 @@ static double dShat_dk(double k, double beta) {
   return dSdb / (2.0 * beta);
 }
 
-static void coarse_tables_impl(const double L[3], const int nl[3], int l, double a, double* T,
-                               double* V) {
+static void coarse_tables_impl(const Smooth& sm, const double L[3], const int nl[3], int l,
+                               double a, double* T, double* V) {
   const double Rl = std::ldexp(a, l - 1);
   const double vol = L[0] * L[1] * L[2];
   const double Rc = std::max(3.8 * std::cbrt(vol), Rl);
@@ -184,8 +210,8 @@ static void coarse_tables_impl(const double L[3], const int nl[3], int l, double
           } else {
             double S, dS;
             smooth_part(r, beta, &S, &dS);
-            f = sgamma(Rl, r) - S;
-            fp = sdgamma_over_r(Rl, r) - dS;
+            f = sgamma(sm, Rl, r) - S;
+            fp = sdgamma_over_r(sm, Rl, r) - dS;
           }
           t += f;
           w[0] += fp * r3[0] * r3[0];
@@ -237,7 +263,8 @@ static void free_plan(Plan* p) {
   void* ptrs[] = {p->d_pos_w, p->d_cell_of, p->d_cell_count, p->d_cell_start, p->d_sorted,
                   p->d_sorted_idx, p->d_e0, p->d_floc, p->d_rows, p->d_wv, p->d_top_T,
                   p->d_top_V, p->d_epart, p->d_wpart, p->d_out, p->d_flag, p->d_scan,
-                  p->d_q1fx, p->d_tcw, p->d_lbw, p->d_lbpot};
+                  p->d_q1fx, p->d_tcw, p->d_lbw, p->d_lbpot, p->d_mma_rows, p->d_mma_bv,
+                  p->d_mma_be};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 1; k <= kMaxLevels; ++k) {
@@ -276,7 +303,7 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
     if (!(box[d] > 0.0) || !std::isfinite(box[d])) return MLS6_ERR_BOX;
     if (nl[d] < 1) return MLS6_ERR_GRID;
   }
-  coarse_tables_impl(box, nl, levels, a, T, V);
+  coarse_tables_impl(smooth_coefficients(2), box, nl, levels, a, T, V);
   return MLS6_OK;
 }
 
@@ -297,8 +324,14 @@ int mls6_auto_levels(const double box[3], double h) {
 
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision) {
+  return mls6_plan_smooth(out, box, N, a, h, levels, order, precision, 2);
+}
+
+int mls6_plan_smooth(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
+                     int levels, int order, int precision, int continuity) {
   if (!out) return MLS6_ERR_ARG;
   *out = nullptr;
+  if (continuity < 1 || continuity > 4) return MLS6_ERR_ARG;
   if (!box || N < 0 || N > (int64_t)1 << 30 || !(a > 0.0) || !std::isfinite(a)) return MLS6_ERR_ARG;
   if (precision != MLS6_FP64 && precision != MLS6_FP32 && precision != MLS6_MIXED)
     return MLS6_ERR_ARG;
@@ -319,7 +352,8 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
   p->prec = precision;
   p->N = N;
   p->stream = 0;
-  p->c_self = gamma_fn(0.0) / std::pow(a, 6.0);
+  p->sm = smooth_coefficients(continuity);
+  p->c_self = gamma_fn(p->sm, 0.0) / std::pow(a, 6.0);
   for (int k = 1; k <= levels; ++k) {
     Level& lv = p->lv[k];
     lv.np = 1;
@@ -362,8 +396,8 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
         for (int dx = -R; dx <= R; ++dx) {
           double r3[3] = {dx * h[0], dy * h[1], dz * h[2]};
           double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
-          double G = r > 0.0 ? dg_level_over_r(1, levels, a, r) : 0.0;
-          p->h_wv.push_back(g_level(1, levels, a, r));
+          double G = r > 0.0 ? dg_level_over_r(p->sm, 1, levels, a, r) : 0.0;
+          p->h_wv.push_back(g_level(p->sm, 1, levels, a, r));
           p->h_wv.push_back(G);
           p->h_wv.push_back(G * dx);
           p->h_wv.push_back(G * dx * dx);
@@ -377,7 +411,7 @@ int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, doubl
   const Level& top = p->lv[levels];
   p->h_top_T.assign((size_t)top.np, 0.0);
   p->h_top_V.assign((size_t)top.np * 6, 0.0);
-  coarse_tables_impl(box, top.n, levels, a, p->h_top_T.data(), p->h_top_V.data());
+  coarse_tables_impl(p->sm, box, top.n, levels, a, p->h_top_T.data(), p->h_top_V.data());
 
   rc = upload_tables(p);
   if (rc) {
@@ -414,7 +448,7 @@ int mls6_last_error(mls6_plan_t* plan) {
   int flag = 0;
   if (cudaMemcpy(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return MLS6_ERR_CUDA;
-  return flag ? MLS6_ERR_NONFINITE : MLS6_OK;
+  return flag_status(flag);
 }
 
 int mls6_plan_info(const mls6_plan_t* plan, int* n_grid, double* h_actual, int* levels,
@@ -435,7 +469,7 @@ int mls6_set_tuning(mls6_plan_t* plan, int split, int groups) {
   if (!plan) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8 && split != 16 &&
-      split != 32)
+      split != 32 && split != 128 && split != 256 && split != 512)
     return MLS6_ERR_ARG;
   if (split > 8 && !pair_cluster_ok(p)) return MLS6_ERR_ARG;
   if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return MLS6_ERR_ARG;
@@ -463,7 +497,7 @@ int mls6_stencil_kind(const mls6_plan_t* plan) {
   if (!plan) return MLS6_ERR_ARG;
   const Plan* p = reinterpret_cast<const Plan*>(plan);
   if (p->levels < 2) return -1;
-  return p->stencil_tc ? 2 : (p->stencil_global ? 1 : 0);
+  return p->stencil_mma ? 3 : p->stencil_tc ? 2 : (p->stencil_global ? 1 : 0);
 }
 
 int mls6_get_tuning(const mls6_plan_t* plan, int* split, int* groups) {
@@ -485,7 +519,7 @@ const char* mls6_status_string(int s) {
     case MLS6_ERR_ORDER: return "unsupported interpolation order (only 3)";
     case MLS6_ERR_CUDA: return "CUDA runtime error";
     case MLS6_ERR_NOMEM: return "device allocation failed";
-    case MLS6_ERR_TIMEOUT: return "device wait timed out";
+    case MLS6_ERR_TIMEOUT: return "a bounded device-side wait ran out (the kernel gave up)";
     case MLS6_ERR_NONFINITE: return "non-finite position or coefficient";
     case MLS6_ERR_SIZE: return "size exceeds a fixed capacity";
     default: return "unknown status";

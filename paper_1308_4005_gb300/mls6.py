@@ -32,7 +32,8 @@ _PREC = {"fp64": MLS6_FP64, "fp32": MLS6_FP32, "mixed": MLS6_MIXED,
          MLS6_FP64: MLS6_FP64, MLS6_FP32: MLS6_FP32, MLS6_MIXED: MLS6_MIXED}
 
 # every symbol declared in include/mls6.h
-EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_set_stream",
+EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_plan_smooth",
+           "mls6_set_stream",
            "mls6_set_graph", "mls6_eval",
            "mls6_eval_atoms", "mls6_eval_lb", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
            "mls6_profile", "mls6_stage_times", "mls6_stage_name", "mls6_auto_levels",
@@ -73,6 +74,9 @@ def load(path: str = LIB_PATH):
     L.mls6_plan.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
                             C.c_int, C.c_int, C.c_int]
     L.mls6_plan.restype = C.c_int
+    L.mls6_plan_smooth.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
+                                   C.c_int, C.c_int, C.c_int, C.c_int]
+    L.mls6_plan_smooth.restype = C.c_int
     L.mls6_set_stream.argtypes = [C.c_void_p, C.c_void_p]
     L.mls6_set_stream.restype = C.c_int
     L.mls6_set_graph.argtypes = [C.c_void_p, C.c_int]
@@ -205,6 +209,15 @@ def mls6_plan(box, N, a, h, levels, order=3, precision=MLS6_FP64):
     out = C.c_void_p()
     _check(load().mls6_plan(C.byref(out), _darr(box), int(N), float(a), float(h), int(levels),
                             int(order), int(precision)), "mls6_plan")
+    return out.value
+
+
+def mls6_plan_smooth(box, N, a, h, levels, order=3, precision=MLS6_FP64, continuity=2):
+    """As mls6_plan with a C^continuity smoothing function (1..4)."""
+    out = C.c_void_p()
+    _check(load().mls6_plan_smooth(C.byref(out), _darr(box), int(N), float(a), float(h),
+                                   int(levels), int(order), int(precision), int(continuity)),
+           "mls6_plan_smooth")
     return out.value
 
 
@@ -405,9 +418,12 @@ class Plan:
     F a new (N, 3) CUDA tensor.  Only marshalling happens here.
     """
 
-    def __init__(self, box, N, a, h, levels, precision="fp64", order=3, stream=None):
+    def __init__(self, box, N, a, h, levels, precision="fp64", order=3, stream=None,
+                 continuity=2):
         self.precision = _PREC[precision]
-        self.handle = mls6_plan(box, N, a, h, levels, order, self.precision)
+        self.handle = (mls6_plan(box, N, a, h, levels, order, self.precision) if continuity == 2
+                       else mls6_plan_smooth(box, N, a, h, levels, order, self.precision,
+                                             continuity))
         self.N = int(N)
         self.box = tuple(float(v) for v in box)
         if stream is not None:

@@ -140,8 +140,9 @@ SHAPE_PARAMS = [c + ("fp64",) for c in SHAPE_CASES] + [
                          ids=[f"{c[0]}-{c[-1]}" for c in SHAPE_PARAMS])
 def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
     """Every pair-kernel shape (lanes per atom 1..8: one atom per lane
-    group; 16, 32: warp form) against the oracle; the warp form is refused
-    where the neighbour range is too wide for it."""
+    group; 16, 32: warp form; 128, 256, 512: queue form with 2, 4, 8 atoms
+    per warp) against the oracle; the warp and queue forms are refused
+    where the neighbour range is too wide for them."""
     import torch
 
     region = None
@@ -156,7 +157,7 @@ def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
     pos = torch.tensor(np.c_[x, c], dtype=dt, device="cuda")
     tol = TOL64 if prec == "fp64" else TOL32
     ran = []
-    for split in (1, 2, 4, 8, 16, 32):
+    for split in (1, 2, 4, 8, 16, 32, 128, 256, 512):
         try:
             gpu_lib.mls6_set_tuning(plan.handle, split, 0)
         except gpu_lib.MLS6Error:
@@ -173,7 +174,7 @@ def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
         ran.append(split)
     assert ran[:4] == [1, 2, 4, 8]
     if name in ("slab_5_levels", "many_tiles"):
-        assert ran[4:] == [16, 32]
+        assert ran[4:] == [16, 32, 128, 256, 512]
 
 
 def test_virial_strain_derivative_many_blocks(gpu_lib):

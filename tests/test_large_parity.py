@@ -86,7 +86,7 @@ def test_cube1m_mixed_full(gpu_lib, cube1m):
     hi+lo operands (2a/h_1 = 6.3 < 9), everything else as FP32."""
     w, x, c, o = cube1m
     g = _gpu(gpu_lib, w, x, c, "mixed")
-    assert g["plan"].info()["stencil_kind"] == 2
+    assert g["plan"].info()["stencil_kind"] == 3  # tcgen05 tensor cores
     _check(g, o, TOLMIX, w.levels, "cube1m/mixed")
 
 

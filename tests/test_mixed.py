@@ -60,7 +60,7 @@ def test_mixed_vs_oracle(gpu_lib, orc, name, N, box, a, h, l):
     g = run(gpu_lib, box, a, h, l, x, c)
     info = g["plan"].info()
     assert info["levels"] == l
-    assert info["stencil_kind"] == 2  # tensor cores
+    assert info["stencil_kind"] == 3  # tcgen05 tensor cores
     dE, dF, dW = errs(g, o)
     assert dE <= TOLMIX["E"], (name, dE)
     assert dF <= TOLMIX["F"], (name, dF)

@@ -527,3 +527,85 @@ def test_eval_sample_equals_eval(orc, case):
     assert -0.5 * np.sum(c * e0) == pytest.approx(le[0], rel=1e-13)
     # the local forces alone sum to zero (pair antisymmetry)
     assert np.abs(Fl.sum(axis=0)).max() <= 1e-12 * np.abs(Fl).max()
+
+
+# ------------------------------------------------ smoothing functions of other continuity
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_smoothing_continuity_order(orc, n):
+    """gamma_n (Sec. II.A.3, compared for C^1..C^4 in Sec. III.B) meets rho^-6
+    at rho = 1 with exactly n continuous derivatives: gamma_n - rho^-6
+    vanishes like (1 - rho)^(n+1) from the left (log-log slope n+1, nonzero
+    limit), equals rho^-6 on the right, and its derivative routine matches
+    finite differences."""
+    with orc.smoothing_order(n):
+        ts = [0.005, 0.0025, 0.00125]
+        d = [orc.gamma(1 - t) - (1 - t) ** -6 for t in ts]
+        for k in range(2):
+            slope = math.log(abs(d[k] / d[k + 1])) / math.log(2.0)
+            assert slope == pytest.approx(n + 1, abs=0.08)
+        assert abs(d[-1] / ts[-1] ** (n + 1)) > 1.0
+        for rho in (1.0, 1.3, 2.0):
+            assert orc.gamma(rho) == pytest.approx(rho ** -6, rel=1e-15)
+        for rho in (0.2, 0.7, 0.95):
+            fd = (orc.gamma(rho + 1e-6) - orc.gamma(rho - 1e-6)) / 2e-6
+            assert orc.dgamma(rho) == pytest.approx(fd, rel=1e-7, abs=1e-8)
+
+
+@pytest.mark.parametrize("n,gamma0", [(1, 3 / 2), (2, 15 / 8), (3, 35 / 16), (4, 315 / 128)])
+def test_smoothing_self_term_and_telescoping(orc, n, gamma0):
+    """gamma_n(0) is the order-n partial sum of the binomial series of
+    (1 - x)^(-1/2) at x = 1, i.e. prod_{j=1..n} (2j+1)/(2j) (3/2, 15/8, 35/16,
+    315/128); the split still telescopes to r^-6 and sum_{k>=1} g_k(0) =
+    gamma_n(0)/a^6 for every n."""
+    assert gamma0 == pytest.approx(math.prod((2 * j + 1) / (2 * j) for j in range(1, n + 1)))
+    a, l = 2.5, 4
+    with orc.smoothing_order(n):
+        assert orc.gamma(0.0) == gamma0
+        rng = np.random.default_rng(n)
+        for r in rng.uniform(0.3, 40.0, 300):
+            s = sum(orc.gk(k, l, a, r) for k in range(l + 1))
+            assert s == pytest.approx(r ** -6, rel=1e-12)
+        assert sum(orc.gk(k, l, a, 0.0) for k in range(1, l + 1)) == pytest.approx(
+            gamma0 / a ** 6, rel=1e-14)
+    assert orc.smoothing() == 2
+
+
+@pytest.mark.parametrize("n", [1, 3, 4])
+def test_smoothing_variants_exact_on_coarsest_lattice(orc, n):
+    """Whatever gamma, atoms on a lattice commensurate with the coarsest grid
+    make every transfer an injection, so the MLS energy equals the exact
+    lattice sum (E/N = -1/2 c^2 S / s^6, S = 8.40192... for simple cubic)."""
+    L, levels, h, a = 8.0, 3, 1.0, 2.0
+    s = 4 * h
+    m = int(L / s)
+    x = np.array([[i, j, k] for i in range(m) for j in range(m) for k in range(m)], float) * s
+    c = np.full(len(x), 1.1)
+    nn = orc.grid_dims((L, L, L), h, levels)
+    with orc.smoothing_order(n):
+        o = orc.evaluate((L, L, L), a, nn, levels, x, c)
+    S = 8.40192397482754
+    assert o["E"] / len(x) == pytest.approx(-0.5 * 1.21 * S / s ** 6, rel=1e-10)
+    assert np.abs(o["F"]).max() < 1e-12
+
+
+def test_smoothing_variants_converge_with_cutoff(orc):
+    """Every C^n MLS converges to the exact periodic forces as the cutoff
+    grows at fixed a/h (Sec. III.B bounds ~ h^n / a^(n+7)).  (The paper's
+    figure also shows C^1 converging more slowly than C^2 on its slab; on
+    this small cube the two rates are within 5% and no ordering is
+    asserted.)"""
+    box = (9.0, 9.0, 9.0)
+    x, c = I.uniform_atoms(808, 300, box)
+    ex = orc.brute(box, x, c, r_img=10 * 9.0)["F"]
+    errs = {}
+    for n in (1, 2, 3, 4):
+        with orc.smoothing_order(n):
+            e = []
+            for a in (1.5, 2.25):
+                h = a / 3.0
+                nn = orc.grid_dims(box, h, 2)
+                F = orc.evaluate(box, a, nn, 2, x, c)["F"]
+                e.append(np.linalg.norm(F - ex) / np.linalg.norm(ex))
+            errs[n] = e
+            assert e[1] < 0.2 * e[0]
