@@ -111,17 +111,31 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision);
 
-/* As mls6_plan, with a smoothing function of continuity C^n,
- * n = continuity in 1..4 (mls6_plan uses n = 2, Eq. gamma).  The paper
- * builds gamma from the electrostatic smoothing functions (Sec. II.A.3) and
- * compares C^1 .. C^4 (Sec. III.B) but prints only n = 2; with u = rho^12,
- * rho^-6 = u^(-1/2), and gamma_n is its Taylor polynomial about u = 1 to
- * order n (n = 2 reproduces Eq. gamma), rho^-6 for rho >= 1.  It changes
- * g_0 .. g_l, the tables and the self term gamma_n(0)/a^6.  Plans with
- * n != 2 run the per-atom pair kernel only (pair_split 1..8) and refuse
- * mls6_eval_lb (MLS6_ERR_ARG).  continuity outside 1..4: MLS6_ERR_ARG. */
-int mls6_plan_smooth(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
-                     int levels, int order, int precision, int continuity);
+/* Plan options beyond mls6_plan's arguments (zero-initialise for the
+ * defaults).
+ *   continuity  C^n smoothing function, n in 1..4; 0 means 2 (Eq. gamma).
+ *               The paper builds gamma from the electrostatic smoothing
+ *               functions (Sec. II.A.3) and compares C^1 .. C^4 (Sec. III.B)
+ *               but prints only n = 2; with u = rho^12, rho^-6 = u^(-1/2) and
+ *               gamma_n is its Taylor polynomial about u = 1 to order n
+ *               (n = 2 reproduces Eq. gamma), rho^-6 for rho >= 1.  It
+ *               changes g_0 .. g_l, the tables and the self term
+ *               gamma_n(0)/a^6.  Plans with n != 2 run the per-atom pair
+ *               kernel only (pair_split 1..8) and refuse mls6_eval_lb.
+ *   stencil     level-stencil kernel of an MLS6_MIXED plan: 0 automatic
+ *               (tcgen05 tensor cores when 2a/h_1 < 9 and the levels give
+ *               at least two 16^3 tiles per SM of the device, else the FP32
+ *               CUDA-core kernel), 1 the FP32 CUDA-core kernel, 2 tcgen05
+ *               tensor cores whenever 2a/h_1 < 9.  Ignored in FP64 / FP32.
+ * Out-of-range values return MLS6_ERR_ARG. */
+typedef struct {
+  int continuity;
+  int stencil;
+} mls6_plan_options;
+
+/* As mls6_plan, with options (NULL = defaults). */
+int mls6_plan_ex(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
+                 int levels, int order, int precision, const mls6_plan_options* opts);
 
 /* Enqueue subsequent work of the plan on a cudaStream_t (NULL = legacy
  * default stream).  Internally an evaluation runs on two streams owned by
@@ -247,10 +261,12 @@ int mls6_auto_levels(const double box[3], double h);
 int mls6_set_tuning(mls6_plan_t* p, int pair_split, int stencil_groups);
 
 /* Which level-stencil kernel the plan runs: 0 shared-memory tiles on the
- * CUDA cores (FP64 / FP32), 1 global-memory fallback (tile and taps beyond
- * the shared-memory budget), 2 tensor cores through mma.sync (MLS6_MIXED,
- * not chosen while 3 applies), 3 tensor cores through tcgen05 with the
- * accumulators in tensor memory (MLS6_MIXED, 2a/h_1 < 9), -1 none (l = 1). */
+ * CUDA cores (FP64 / FP32, and MLS6_MIXED plans whose grids are too small
+ * for the tensor-core tiles), 1 global-memory fallback (tile and taps
+ * beyond the shared-memory budget), 2 tensor cores through mma.sync
+ * (MLS6_MIXED, not chosen while 3 applies), 3 tensor cores through tcgen05
+ * with the accumulators in tensor memory (MLS6_MIXED, 2a/h_1 < 9, see
+ * mls6_plan_options), -1 none (l = 1). */
 int mls6_stencil_kind(const mls6_plan_t* p);
 int mls6_get_tuning(const mls6_plan_t* p, int* pair_split, int* stencil_groups);
 

@@ -56,6 +56,12 @@ static bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+static int dev_of(const Plan*) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+
 template <typename T> static int upload_tables_t(Plan* p) {
   const long N = p->N;
   const size_t e = sizeof(T);
@@ -97,13 +103,20 @@ template <typename T> static int upload_tables_t(Plan* p) {
   if (rc) return rc;
   rc = prepare_pair_kernels<T>(p);
   if (rc) return rc;
-  if (stencil_mma_eligible(p)) {  // mixed precision: tcgen05 stencil tiles
+  // mixed precision: tcgen05 stencil tiles, unless the grids give fewer than
+  // two tiles per SM (the FP32 kernel's 8^3 tiles fill the device better:
+  // 65,536-atom slab 35 vs 61 us) or the caller asked for the CUDA cores
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_of(p));
+  const bool want_mma = p->stencil_req == 2 ||
+                        (p->stencil_req == 0 && stencil_mma_tiles(p) >= 2L * std::max(sms, 1));
+  if (want_mma && stencil_mma_eligible(p)) {
     stencil_mma_geometry(p);
     p->stencil_mma = true;
     p->stencil_global = false;
     rc = prepare_stencil_mma(p);
     if (rc) return rc;
-  } else if (stencil_tc_eligible(p)) {  // mixed precision: mma.sync stencil tiles
+  } else if (p->stencil_req == 2 && stencil_tc_eligible(p)) {  // mma.sync stencil tiles
     tc_geometry(p);
     p->stencil_tc = true;
     p->stencil_global = false;

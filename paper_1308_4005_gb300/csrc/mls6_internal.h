@@ -91,6 +91,7 @@ struct Plan {
   bool stencil_tc = false;      // mma.sync tensor-core stencil (mixed precision)
   uint32_t* d_tcw = nullptr;    // its packed split weight pairs
   bool stencil_mma = false;     // tcgen05 tensor-core stencil (mixed precision)
+  int stencil_req = 0;          // mls6_plan_options::stencil
   int mma_rows_pad_v = 0, mma_rows_pad_e = 0;  // tap rows padded to whole chunks
   int* d_mma_rows = nullptr;    // padded row table (int4: dy, dz, R, first)
   uint8_t* d_mma_bv = nullptr;  // B matrices, energy + six virial channels
@@ -208,6 +209,7 @@ int prepare_stencil_tc(Plan* p);
 int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st);
 // tcgen05 stencil (mls6_stencil_mma.cu)
 bool stencil_mma_eligible(const Plan* p);
+long stencil_mma_tiles(const Plan* p);
 void stencil_mma_geometry(Plan* p);
 int prepare_stencil_mma(Plan* p);
 int launch_stencil_mma(Plan* p, bool vir, bool fuse_top, cudaStream_t st);

@@ -324,14 +324,16 @@ int mls6_auto_levels(const double box[3], double h) {
 
 int mls6_plan(mls6_plan_t** out, const double box[3], int64_t N, double a, double h, int levels,
               int order, int precision) {
-  return mls6_plan_smooth(out, box, N, a, h, levels, order, precision, 2);
+  return mls6_plan_ex(out, box, N, a, h, levels, order, precision, nullptr);
 }
 
-int mls6_plan_smooth(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
-                     int levels, int order, int precision, int continuity) {
+int mls6_plan_ex(mls6_plan_t** out, const double box[3], int64_t N, double a, double h,
+                 int levels, int order, int precision, const mls6_plan_options* opts) {
   if (!out) return MLS6_ERR_ARG;
   *out = nullptr;
-  if (continuity < 1 || continuity > 4) return MLS6_ERR_ARG;
+  const int continuity = (opts && opts->continuity) ? opts->continuity : 2;
+  const int stencil = opts ? opts->stencil : 0;
+  if (continuity < 1 || continuity > 4 || stencil < 0 || stencil > 2) return MLS6_ERR_ARG;
   if (!box || N < 0 || N > (int64_t)1 << 30 || !(a > 0.0) || !std::isfinite(a)) return MLS6_ERR_ARG;
   if (precision != MLS6_FP64 && precision != MLS6_FP32 && precision != MLS6_MIXED)
     return MLS6_ERR_ARG;
@@ -353,6 +355,7 @@ int mls6_plan_smooth(mls6_plan_t** out, const double box[3], int64_t N, double a
   p->N = N;
   p->stream = 0;
   p->sm = smooth_coefficients(continuity);
+  p->stencil_req = stencil;
   p->c_self = gamma_fn(p->sm, 0.0) / std::pow(a, 6.0);
   for (int k = 1; k <= levels; ++k) {
     Level& lv = p->lv[k];

@@ -444,6 +444,14 @@ bool stencil_mma_eligible(const Plan* p) {
   return mma_smem<true>(p->P) + 4096 <= 227 * 1024;
 }
 
+// Number of 16^3 tiles over the levels k < l.
+long stencil_mma_tiles(const Plan* p) {
+  long t = 0;
+  for (int k = 1; k < p->levels; ++k)
+    t += cdiv(p->lv[k].n[0], kMmaX) * cdiv(p->lv[k].n[1], kMmaY) * cdiv(p->lv[k].n[2], kMmaZ);
+  return t;
+}
+
 // Tile geometry (16 x 16 x 16 nodes per block).
 void stencil_mma_geometry(Plan* p) {
   p->stencil_blocks = 0;

@@ -32,7 +32,7 @@ _PREC = {"fp64": MLS6_FP64, "fp32": MLS6_FP32, "mixed": MLS6_MIXED,
          MLS6_FP64: MLS6_FP64, MLS6_FP32: MLS6_FP32, MLS6_MIXED: MLS6_MIXED}
 
 # every symbol declared in include/mls6.h
-EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_plan_smooth",
+EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_plan_ex",
            "mls6_set_stream",
            "mls6_set_graph", "mls6_eval",
            "mls6_eval_atoms", "mls6_eval_lb", "mls6_last_error", "mls6_plan_info", "mls6_debug_grid",
@@ -74,9 +74,9 @@ def load(path: str = LIB_PATH):
     L.mls6_plan.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
                             C.c_int, C.c_int, C.c_int]
     L.mls6_plan.restype = C.c_int
-    L.mls6_plan_smooth.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
-                                   C.c_int, C.c_int, C.c_int, C.c_int]
-    L.mls6_plan_smooth.restype = C.c_int
+    L.mls6_plan_ex.argtypes = [C.POINTER(C.c_void_p), _dp, C.c_int64, C.c_double, C.c_double,
+                               C.c_int, C.c_int, C.c_int, C.POINTER(PlanOptions)]
+    L.mls6_plan_ex.restype = C.c_int
     L.mls6_set_stream.argtypes = [C.c_void_p, C.c_void_p]
     L.mls6_set_stream.restype = C.c_int
     L.mls6_set_graph.argtypes = [C.c_void_p, C.c_int]
@@ -212,12 +212,23 @@ def mls6_plan(box, N, a, h, levels, order=3, precision=MLS6_FP64):
     return out.value
 
 
-def mls6_plan_smooth(box, N, a, h, levels, order=3, precision=MLS6_FP64, continuity=2):
-    """As mls6_plan with a C^continuity smoothing function (1..4)."""
+class PlanOptions(C.Structure):
+    """mls6_plan_options: continuity (0 = 2), stencil (0 auto, 1 CUDA cores,
+    2 tcgen05 tensor cores; mixed precision only)."""
+    _fields_ = [("continuity", C.c_int), ("stencil", C.c_int)]
+
+
+_STENCIL = {"auto": 0, "cuda": 1, "tensor": 2, 0: 0, 1: 1, 2: 2}
+
+
+def mls6_plan_ex(box, N, a, h, levels, order=3, precision=MLS6_FP64, continuity=2,
+                 stencil="auto"):
+    """As mls6_plan with options (smoothing continuity, stencil kernel)."""
     out = C.c_void_p()
-    _check(load().mls6_plan_smooth(C.byref(out), _darr(box), int(N), float(a), float(h),
-                                   int(levels), int(order), int(precision), int(continuity)),
-           "mls6_plan_smooth")
+    opt = PlanOptions(int(continuity), _STENCIL[stencil])
+    _check(load().mls6_plan_ex(C.byref(out), _darr(box), int(N), float(a), float(h),
+                               int(levels), int(order), int(precision), C.byref(opt)),
+           "mls6_plan_ex")
     return out.value
 
 
@@ -419,11 +430,13 @@ class Plan:
     """
 
     def __init__(self, box, N, a, h, levels, precision="fp64", order=3, stream=None,
-                 continuity=2):
+                 continuity=2, stencil="auto"):
         self.precision = _PREC[precision]
-        self.handle = (mls6_plan(box, N, a, h, levels, order, self.precision) if continuity == 2
-                       else mls6_plan_smooth(box, N, a, h, levels, order, self.precision,
-                                             continuity))
+        if continuity == 2 and stencil == "auto":
+            self.handle = mls6_plan(box, N, a, h, levels, order, self.precision)
+        else:
+            self.handle = mls6_plan_ex(box, N, a, h, levels, order, self.precision, continuity,
+                                       stencil)
         self.N = int(N)
         self.box = tuple(float(v) for v in box)
         if stream is not None:

@@ -73,8 +73,9 @@ def test_plan_argument_validation_needs_no_gpu(lib):
     bad = mls6._darr((10.0, -1.0, 10.0))
     assert lib.mls6_plan(C.byref(h), bad, 100, 2.5, 1.0, 3, 3, 0) == mls6.MLS6_ERR_BOX
     assert lib.mls6_plan(None, box, 100, 2.5, 1.0, 3, 3, 0) == mls6.MLS6_ERR_ARG
-    for n in (0, 5, -2):  # smoothing continuity outside 1..4
-        assert lib.mls6_plan_smooth(C.byref(h), box, 100, 2.5, 1.0, 3, 3, 0, n) == \
+    for n, st in ((5, 0), (-2, 0), (2, 3), (2, -1)):  # options out of range
+        opt = mls6.PlanOptions(n, st)
+        assert lib.mls6_plan_ex(C.byref(h), box, 100, 2.5, 1.0, 3, 3, 0, C.byref(opt)) == \
             mls6.MLS6_ERR_ARG
     assert mls6.status_string(mls6.MLS6_ERR_NONFINITE).startswith("non-finite")
     assert mls6.status_string(mls6.MLS6_ERR_TIMEOUT).startswith("a bounded")

@@ -24,7 +24,8 @@ TOLMIX = dict(E=2e-5, F=1e-4, W=5e-5)
 def run(gpu_lib, box, a, h, l, x, c, prec="mixed", virial=True):
     import torch
 
-    plan = gpu_lib.Plan(box, len(c), a, h, l, precision=prec)
+    # these grids are small: ask for the tensor-core stencil explicitly
+    plan = gpu_lib.Plan(box, len(c), a, h, l, precision=prec, stencil="tensor")
     pos = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
     r = plan.evaluate(pos, virial=virial)
     torch.cuda.synchronize()
@@ -101,3 +102,19 @@ def test_mixed_wide_stencil_uses_fp32_path(gpu_lib, orc):
     assert gm["E"] == gf["E"] and np.array_equal(gm["F"], gf["F"])
     dE, dF, dW = errs(gm, o)
     assert dE <= 2e-6 and dF <= 1e-4 and dW <= 2e-5
+
+
+def test_mixed_stencil_choice_by_grid_size(gpu_lib):
+    """Automatic choice: the tcgen05 stencil when the levels give at least
+    two 16^3 tiles per SM (the 1M-atom cube's 112^3 grid), the FP32 CUDA-core
+    stencil for the 65,536-atom slab's 32 x 32 x 96 grid; both on request."""
+    w = I.workload("slab65536")
+    auto = gpu_lib.Plan(w.box, w.N, w.a, w.h, w.levels, precision="mixed")
+    assert auto.info()["stencil_kind"] == 0
+    forced = gpu_lib.Plan(w.box, w.N, w.a, w.h, w.levels, precision="mixed", stencil="tensor")
+    assert forced.info()["stencil_kind"] == 3
+    c = I.workload("cube1m")
+    big = gpu_lib.Plan(c.box, 1000, c.a, c.h, c.levels, precision="mixed")
+    assert big.info()["stencil_kind"] == 3
+    cuda = gpu_lib.Plan(c.box, 1000, c.a, c.h, c.levels, precision="mixed", stencil="cuda")
+    assert cuda.info()["stencil_kind"] == 0

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 def _run(gpu_lib, box, a, h, l, x, c, prec, n):
     import torch
 
-    plan = gpu_lib.Plan(box, len(c), a, h, l, precision=prec, continuity=n)
+    plan = gpu_lib.Plan(box, len(c), a, h, l, precision=prec, continuity=n, stencil="tensor")
     dt = torch.float64 if prec == "fp64" else torch.float32
     r = plan.evaluate(torch.tensor(np.c_[x, c], dtype=dt, device="cuda"), virial=True)
     torch.cuda.synchronize()
