@@ -24,6 +24,9 @@
  *     windowed-out remainder (compensated summation over the images).
  *  R8 virial: strain derivative with grids deforming with the cell.
  *  R9 cutoff tests are strict (r < cutoff); g_k is exactly 0 beyond.
+ *  R10 interpolation order p = 5 uses the C^1 quintic below (the paper
+ *     compares p = 5 but prints only the cubic); parity unpinned against
+ *     the paper for p = 5: it is pinned to its defining conditions.
  */
 #include "mls6_oracle.h"
 
@@ -119,9 +122,35 @@ double orc_dgk(int k, int l, double a, double r) {
   return pow(s_in, -7.0) * orc_dgamma(r / s_in) - pow(s_out, -7.0) * orc_dgamma(r / s_out);
 }
 
-/* Eq. (Phi-Hermite): the cubic nodal basis function with support |t| < 2. */
+/* Nodal basis functions (Eq. def-phi).  Order p = 3 is Eq. (Phi-Hermite),
+ * the cubic C^1 interpolant with support |t| < 2.  Order p = 5 (Sec. III.B
+ * compares p = 3 and p = 5 without printing the p = 5 function) is read as
+ * the C^1 quintic of the electrostatic multilevel method the paper takes its
+ * interpolants from (Hardy 2006): even, piecewise quintic on the unit
+ * intervals, support |t| < 3, interpolating (Phi(0) = 1, Phi(+-1) =
+ * Phi(+-2) = 0), C^1, and reproducing polynomials of degree <= 4 (order 5).
+ * Those conditions leave one free coefficient; the member taken is the one
+ * whose outer piece is a product of linear factors (roots 1, 2, 3, 3, 4),
+ * i.e. (reading R10)
+ *   |t| <= 1:  (1 - t^2)(2 - t)(6 + 3t - 5t^2) / 12
+ *   1..2:      (t - 1)(t - 2)(t - 3)(5t^2 - 9t - 4) / 24
+ *   2..3:     -(t - 1)(t - 2)(t - 3)^2 (t - 4) / 24       (t = |t| here). */
+static int g_order = 3;
+
+void orc_set_order(int p) { g_order = p == 5 ? 5 : 3; }
+int orc_get_order(void) { return g_order; }
+
+/* half-width of the support of Phi: nodes m with |t - m| < S contribute */
+static double supp(void) { return g_order == 5 ? 3.0 : 2.0; }
+
 double orc_Phi(double t) {
   double u = fabs(t);
+  if (g_order == 5) {
+    if (u <= 1.0) return (1.0 - u * u) * (2.0 - u) * (6.0 + 3.0 * u - 5.0 * u * u) / 12.0;
+    if (u <= 2.0) return (u - 1.0) * (u - 2.0) * (u - 3.0) * (5.0 * u * u - 9.0 * u - 4.0) / 24.0;
+    if (u <= 3.0) return -(u - 1.0) * (u - 2.0) * (u - 3.0) * (u - 3.0) * (u - 4.0) / 24.0;
+    return 0.0;
+  }
   if (u <= 1.0) return (1.0 - u) * (1.0 + u - 1.5 * t * t);
   if (u <= 2.0) return -0.5 * (u - 1.0) * (2.0 - u) * (2.0 - u);
   return 0.0;
@@ -129,6 +158,14 @@ double orc_Phi(double t) {
 
 double orc_dPhi(double t) {
   double u = fabs(t), sg = t < 0.0 ? -1.0 : 1.0;
+  if (g_order == 5) {
+    /* derivatives of the expanded pieces */
+    if (u <= 1.0) return sg * (-u * (25.0 * u * u * u - 52.0 * u * u - 15.0 * u + 50.0) / 12.0);
+    if (u <= 2.0)
+      return sg * ((((25.0 * u - 156.0) * u + 315.0) * u - 210.0) * u + 10.0) / 24.0;
+    if (u <= 3.0) return sg * (-(u - 3.0) * (((5.0 * u - 37.0) * u + 84.0) * u - 58.0) / 24.0);
+    return 0.0;
+  }
   if (u <= 1.0) return sg * (-5.0 * u + 4.5 * u * u);
   if (u <= 2.0) return sg * (-0.5 * (2.0 - u) * (4.0 - 3.0 * u));
   return 0.0;
@@ -485,12 +522,13 @@ static void local_atom_allpairs(const ctx_t* C, int64_t i, double* e0, double F[
 /* Eq. (anterpolation): xi^1_mu = sum_j phi^1_mu(x_j) xi_j. */
 static void anterpolate(ctx_t* C) {
   const int* n = C->n[1];
+  const double S = supp();
   for (int64_t j = 0; j < C->N; ++j) {
     double u[3];
     for (int d = 0; d < 3; ++d) u[d] = n[d] * C->s[3 * j + d];
-    for (long m0 = (long)ceil(u[0] - 2.0); m0 <= (long)floor(u[0] + 2.0); ++m0)
-      for (long m1 = (long)ceil(u[1] - 2.0); m1 <= (long)floor(u[1] + 2.0); ++m1)
-        for (long m2 = (long)ceil(u[2] - 2.0); m2 <= (long)floor(u[2] + 2.0); ++m2) {
+    for (long m0 = (long)ceil(u[0] - S); m0 <= (long)floor(u[0] + S); ++m0)
+      for (long m1 = (long)ceil(u[1] - S); m1 <= (long)floor(u[1] + S); ++m1)
+        for (long m2 = (long)ceil(u[2] - S); m2 <= (long)floor(u[2] + S); ++m2) {
           double w = orc_Phi(u[0] - m0) * orc_Phi(u[1] - m1) * orc_Phi(u[2] - m2);
           long idx = wrapi(m0, n[0]) + n[0] * (wrapi(m1, n[1]) + n[1] * wrapi(m2, n[2]));
           C->q[1][idx] += w * C->c[j];
@@ -507,13 +545,14 @@ static void restrict_level(ctx_t* C, int k) {
   const int* nc = C->n[k + 1];
   const double* qf = C->q[k];
   double* qc = C->q[k + 1];
+  const long S2 = (long)(2.0 * supp());
 #pragma omp parallel for num_threads(NT) schedule(static)
   for (long mu = 0; mu < C->np[k + 1]; ++mu) {
     long m0 = mu % nc[0], m1 = (mu / nc[0]) % nc[1], m2 = mu / ((long)nc[0] * nc[1]);
     double acc = 0.0;
-    for (long v2 = 2 * m2 - 4; v2 <= 2 * m2 + 4; ++v2)
-      for (long v1 = 2 * m1 - 4; v1 <= 2 * m1 + 4; ++v1)
-        for (long v0 = 2 * m0 - 4; v0 <= 2 * m0 + 4; ++v0) {
+    for (long v2 = 2 * m2 - S2; v2 <= 2 * m2 + S2; ++v2)
+      for (long v1 = 2 * m1 - S2; v1 <= 2 * m1 + S2; ++v1)
+        for (long v0 = 2 * m0 - S2; v0 <= 2 * m0 + S2; ++v0) {
           double w = orc_Phi(0.5 * v0 - m0) * orc_Phi(0.5 * v1 - m1) * orc_Phi(0.5 * v2 - m2);
           if (w == 0.0) continue;
           long idx = wrapi(v0, nf[0]) + nf[0] * (wrapi(v1, nf[1]) + nf[1] * wrapi(v2, nf[2]));
@@ -671,14 +710,15 @@ static void evaluate_top(ctx_t* C) {
 static void prolongate_level(ctx_t* C, int k) {
   const int* nf = C->n[k];
   const int* nc = C->n[k + 1];
+  const double S = supp();
 #pragma omp parallel for num_threads(NT) schedule(static)
   for (long mu = 0; mu < C->np[k]; ++mu) {
     long m0 = mu % nf[0], m1 = (mu / nf[0]) % nf[1], m2 = mu / ((long)nf[0] * nf[1]);
     double p[3] = {0.5 * m0, 0.5 * m1, 0.5 * m2};
     double acc = 0.0;
-    for (long v2 = (long)ceil(p[2] - 2.0); v2 <= (long)floor(p[2] + 2.0); ++v2)
-      for (long v1 = (long)ceil(p[1] - 2.0); v1 <= (long)floor(p[1] + 2.0); ++v1)
-        for (long v0 = (long)ceil(p[0] - 2.0); v0 <= (long)floor(p[0] + 2.0); ++v0) {
+    for (long v2 = (long)ceil(p[2] - S); v2 <= (long)floor(p[2] + S); ++v2)
+      for (long v1 = (long)ceil(p[1] - S); v1 <= (long)floor(p[1] + S); ++v1)
+        for (long v0 = (long)ceil(p[0] - S); v0 <= (long)floor(p[0] + S); ++v0) {
           double w = orc_Phi(p[0] - v0) * orc_Phi(p[1] - v1) * orc_Phi(p[2] - v2);
           if (w == 0.0) continue;
           long idx = wrapi(v0, nc[0]) + nc[0] * (wrapi(v1, nc[1]) + nc[1] * wrapi(v2, nc[2]));
@@ -700,12 +740,13 @@ static void grid_pipeline(ctx_t* C) {
 /* Eq. (interpolation) and its gradient for atom i: e_i and grad e_i. */
 static void interpolate_atom(const ctx_t* C, int64_t i, double* ei, double g[3]) {
   const int* n = C->n[1];
+  const double S = supp();
   double u[3];
   for (int d = 0; d < 3; ++d) u[d] = n[d] * C->s[3 * i + d];
   double acc = 0.0, gs[3] = {0, 0, 0};
-  for (long m0 = (long)ceil(u[0] - 2.0); m0 <= (long)floor(u[0] + 2.0); ++m0)
-    for (long m1 = (long)ceil(u[1] - 2.0); m1 <= (long)floor(u[1] + 2.0); ++m1)
-      for (long m2 = (long)ceil(u[2] - 2.0); m2 <= (long)floor(u[2] + 2.0); ++m2) {
+  for (long m0 = (long)ceil(u[0] - S); m0 <= (long)floor(u[0] + S); ++m0)
+    for (long m1 = (long)ceil(u[1] - S); m1 <= (long)floor(u[1] + S); ++m1)
+      for (long m2 = (long)ceil(u[2] - S); m2 <= (long)floor(u[2] + S); ++m2) {
         long idx = wrapi(m0, n[0]) + n[0] * (wrapi(m1, n[1]) + n[1] * wrapi(m2, n[2]));
         double ev = C->et[1][idx];
         double p0 = orc_Phi(u[0] - m0), p1 = orc_Phi(u[1] - m1), p2 = orc_Phi(u[2] - m2);

@@ -35,12 +35,18 @@ extern "C" {
 void orc_set_smoothing(int n);
 int  orc_get_smoothing(void);
 
+/* Interpolation order p of the nodal basis Phi used by every entry point
+ * below: 3 (default, Eq. Phi-Hermite, cubic, support |t| < 2) or 5 (C^1
+ * quintic, support |t| < 3).  Process-wide setting. */
+void orc_set_order(int p);
+int  orc_get_order(void);
+
 /* Closed forms (Sec. II.A.3-5). */
 double orc_gamma(double rho);                 /* Eq. (gamma), C^n variant */
 double orc_dgamma(double rho);                /* d gamma / d rho */
 double orc_gk(int k, int l, double a, double r);   /* Eqs. (g_0), (g_k), (g_l) */
 double orc_dgk(int k, int l, double a, double r);  /* d g_k / dr */
-double orc_Phi(double t);                     /* Eq. (Phi-Hermite) */
+double orc_Phi(double t);                     /* Eq. (Phi-Hermite), order p */
 double orc_dPhi(double t);                    /* d Phi / dt */
 
 /* Finest-grid size: per axis the multiple of 2^(levels-1) nearest to L/h

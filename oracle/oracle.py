@@ -72,6 +72,10 @@ def lib():
         L.orc_set_smoothing.argtypes = [C.c_int]
         L.orc_get_smoothing.restype = C.c_int
         L.orc_get_smoothing.argtypes = []
+        L.orc_set_order.restype = None
+        L.orc_set_order.argtypes = [C.c_int]
+        L.orc_get_order.restype = C.c_int
+        L.orc_get_order.argtypes = []
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
@@ -121,6 +125,31 @@ class smoothing_order:
 
     def __exit__(self, *exc):
         set_smoothing(self.old)
+
+
+def set_order(p: int) -> None:
+    """Interpolation order p of the nodal basis: 3 (Eq. Phi-Hermite) or 5
+    (the C^1 quintic)."""
+    lib().orc_set_order(int(p))
+
+
+def order() -> int:
+    return int(lib().orc_get_order())
+
+
+class interp_order:
+    """Context manager: evaluate with the order-p nodal basis."""
+
+    def __init__(self, p):
+        self.p = p
+
+    def __enter__(self):
+        self.old = order()
+        set_order(self.p)
+        return self
+
+    def __exit__(self, *exc):
+        set_order(self.old)
 
 
 def set_threads(n: int) -> None:
