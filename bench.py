@@ -695,6 +695,18 @@ def batch_point(torch, mls6, dev, stream, flush, ws, x, c, off, a, steps, tune):
         torch.cuda.synchronize()
         Fb = F.double().cpu().numpy()
         info = bt.info()
+        # the other launch form (graph of kernel chains / one persistent
+        # kernel), timed for the record with the tuned shapes
+        mode = mls6.mls6_batch_mode(bt.handle)
+        forms = {("persistent" if mode else "chains"): ms}
+        mls6.mls6_batch_set_mode(bt.handle, not mode)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step()
+        other = "persistent" if mls6.mls6_batch_mode(bt.handle) else "chains"
+        if other not in forms:
+            forms[other] = statistics.mean(timed_steps(torch, stream, step, steps, flush))
+        mls6.mls6_batch_set_mode(bt.handle, mode)
         rng = np.random.default_rng(17)
         picks = [r for r in range(0, len(ws), 2)][:2] + [r for r in range(1, len(ws), 2)][:2]
         num = den = 0.0
@@ -707,10 +719,47 @@ def batch_point(torch, mls6, dev, stream, flush, ws, x, c, off, a, steps, tune):
         return {"a": a, "h": ws[0].h, "ms": ms, "value": Ntot / (ms / 1e3),
                 "eps_F": math.sqrt(num / den), "replicas": len(ws), "atoms": Ntot,
                 "launches_per_step": int(info["launches"]), "branches": info["branches"],
+                "form": "persistent" if mode else "chains", "ms_by_form": forms,
                 "plan_s": t_plan, "autotune_s": t_tune,
                 "eps_F_sample": "256 atoms of each of replicas " + ", ".join(map(str, picks))}
     finally:
         bt.close()
+
+
+def lb_point(torch, mls6, dev, stream, flush, w, x, steps, prec="fp32"):
+    """Lorentz-Berthelot mixing (Sec. II.D, seven grid channels) on the same
+    positions: sigma_i ~ U[0.85, 1.15], eps_i ~ U[0.5, 1.5] (seeded), energy
+    and forces."""
+    import numpy as np
+
+    rng = np.random.default_rng(1308)
+    sig = rng.uniform(0.85, 1.15, w.N)
+    eps = rng.uniform(0.5, 1.5, w.N)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = mls6.Plan(w.box, w.N, w.a, w.h, w.levels, precision=prec, stream=stream.cuda_stream)
+    try:
+        pos = torch.tensor(np.asarray(x, np.float64), dtype=dt, device=dev).contiguous()
+        ds = torch.tensor(sig, dtype=dt, device=dev)
+        de = torch.tensor(eps, dtype=dt, device=dev)
+        F = torch.empty((w.N, 3), dtype=dt, device=dev)
+        E = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def step():
+            rc = mls6.mls6_eval_lb(plan.handle, pos.data_ptr(), ds.data_ptr(), de.data_ptr(),
+                                   F.data_ptr(), E.data_ptr())
+            if rc:
+                raise mls6.MLS6Error(rc, "mls6_eval_lb")
+
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                step()
+        ms = statistics.mean(timed_steps(torch, stream, step, steps, flush))
+        _, launches = mls6.mls6_stage_times(plan.handle)
+        return {"precision": prec, "ms": ms, "value": w.N / (ms / 1e3), "channels": 7,
+                "launches_per_step": int(launches), "energy": float(E.item()),
+                "species": "sigma ~ U[0.85, 1.15], eps ~ U[0.5, 1.5] (seed 1308)"}
+    finally:
+        plan.close()
 
 
 def run_ours(args):
@@ -837,6 +886,11 @@ def run_ours(args):
         except Exception as e:
             line["batched"] = {"error": repr(e)}
         log(f"batched done at {time.time() - t_start:.0f} s")
+        try:
+            line["lorentz_berthelot"] = lb_point(torch, mls6, dev, stream, flush, w, x, 5)
+        except Exception as e:
+            line["lorentz_berthelot"] = {"error": repr(e)}
+        log(f"Lorentz-Berthelot done at {time.time() - t_start:.0f} s")
         line["at_1e-4"] = at
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.time()

@@ -53,7 +53,7 @@ typedef enum {
   MLS6_ERR_ARG = -1,        /* NULL pointer, N < 0, a <= 0, h <= 0, bad level ... */
   MLS6_ERR_GRID = -2,       /* grid sizes not nested / too many levels */
   MLS6_ERR_BOX = -3,        /* non-positive or non-finite box */
-  MLS6_ERR_ORDER = -4,      /* interpolation order other than 3 */
+  MLS6_ERR_ORDER = -4,      /* interpolation order other than 3 or 5 */
   MLS6_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error) */
   MLS6_ERR_NOMEM = -6,      /* device allocation failed */
   MLS6_ERR_TIMEOUT = -7,    /* a bounded device-side wait ran out (kernel gave up) */
@@ -101,8 +101,18 @@ int mls6_coarse_tables(const double box[3], const int nl[3], int levels, double 
  *              is L/n_1 (mls6_grid_dims)
  *   levels     number of grid levels l (1..12), or 0 for the automatic rule
  *              of mls6_auto_levels
- *   order      interpolation order p, 3 (Eq. Phi-Hermite); other values
- *              return MLS6_ERR_ORDER
+ *   order      interpolation order p of the nodal basis Phi (Eq. def-phi):
+ *              3 = Eq. (Phi-Hermite), the cubic C^1 interpolant (4 nodes per
+ *              axis); 5 = the C^1 quintic (6 nodes per axis) whose orders
+ *              Sec. III.B compares: even, piecewise quintic, support
+ *              |t| < 3, reproducing polynomials of degree <= 4, the member
+ *              whose outer piece continues to a root at |t| = 4:
+ *                |t|<=1: (1-t^2)(2-|t|)(6+3|t|-5t^2)/12
+ *                1..2:   (|t|-1)(|t|-2)(|t|-3)(5t^2-9|t|-4)/24
+ *                2..3:  -(|t|-1)(|t|-2)(|t|-3)^2(|t|-4)/24
+ *              Order-5 plans run the chained launch form in a batch and are
+ *              refused by the learned correction (features are defined on
+ *              the cubic basis).  Other values return MLS6_ERR_ORDER.
  *   precision  an mls6_precision value, passed as a plain int (the ABI has
  *              no options struct; the stream is set with mls6_set_stream)
  *   *out       receives the plan (NULL on error)
@@ -248,13 +258,19 @@ int mls6_auto_levels(const double box[3], double h);
  * 128, 256, 512: queue form (2, 4 or 8 atoms per warp share that stream,
  * staged in shared memory; the lanes test 32 candidates at a time and the
  * pairs inside the cutoff are queued and evaluated 32 at a time on full
- * warps).  The warp and queue forms are refused with MLS6_ERR_ARG when the
- * neighbour range spans more than two cells per side or the box has fewer
- * than five cells along x.  stencil_groups: thread groups of 128 sharing one
- * 8^3 stencil tile (1, 2 or 4; ignored when the stencil tile does not fit in
- * shared memory); 0 keeps the current value.  Defaults: FP64 the queue form
- * with two atoms per warp where allowed; otherwise the lanes per atom that
- * give about 48 resident warps per SM; stencil: 24 warps per SM.  A shape
+ * warps); 1024: cluster form (FP32 and mixed plans: a warp pairs 8
+ * consecutive sorted atoms with every candidate of their segment's
+ * neighbour cells, four candidates per step, branch-free; Lorentz-Berthelot
+ * evaluations of such a plan run the one-lane-per-atom kernel).  The warp
+ * and queue forms are refused with MLS6_ERR_ARG when the neighbour range
+ * spans more than two cells per side or the box has fewer than five cells
+ * along x, the cluster form also in FP64 or with fewer than 16 cells along
+ * x.  stencil_groups: thread groups of 128 sharing one 8^3 stencil tile (1,
+ * 2 or 4; ignored when the stencil tile does not fit in shared memory); 0
+ * keeps the current value.  Defaults: FP64 the queue form with two atoms per
+ * warp where allowed; otherwise the lanes per atom that give about 48
+ * resident warps per SM (the cluster form is selected only by this call);
+ * stencil: 24 warps per SM.  A shape
  * changes the order of floating-point sums (results move at rounding level),
  * never what is summed.  Waits for the plan's streams; the next evaluation
  * re-captures its graph. */
@@ -273,11 +289,13 @@ int mls6_get_tuning(const mls6_plan_t* p, int* pair_split, int* stencil_groups);
 /* ---------------------------------------------------------------------
  * Batches: B independent replicas (each its own box, atom count and grid
  * hierarchy, same a, h, levels rule, order and precision) evaluated by a
- * single CUDA graph launch.  The replicas' kernel sequences are captured
- * into K independent chains of the graph (branches), replicas assigned to
- * chains by longest-processing-time-first on the cost model below.  Each
- * replica runs the kernels of a single plan with the same shapes, so its
- * results equal mls6_eval's on such a plan bit for bit.
+ * single CUDA graph launch.  FP32 batches can run one persistent kernel
+ * instead (see mls6_batch_set_mode); by default the replicas' kernel sequences are
+ * captured into K independent chains of the graph (branches), replicas
+ * assigned to chains by longest-processing-time-first on the cost model
+ * below.  Each replica runs the kernels (or kernel bodies) of a single plan
+ * with the same shapes, so its results equal mls6_eval's on such a plan bit
+ * for bit.
  * --------------------------------------------------------------------- */
 typedef struct mls6_batch_t mls6_batch_t;
 
@@ -321,6 +339,8 @@ int mls6_batch_eval(mls6_batch_t* b, const void* pos, const void* c, void* force
  * with the virial) while it varies the branch count over 1..64, then the
  * lanes per atom and the stencil groups of every replica one power of two
  * below and above their defaults, keeping each change that lowers the time.
+ * For FP32 batches that the persistent kernel can run, the other launch
+ * form (mls6_batch_set_mode) is tuned as well and the faster form is kept.
  * Leaves the best configuration applied; best_sec (may be NULL) receives
  * its time.  forces is overwritten. */
 int mls6_batch_tune(mls6_batch_t* b, const void* pos, const void* c, void* forces, int reps,
@@ -349,6 +369,38 @@ int mls6_batch_replica(mls6_batch_t* b, int r, mls6_plan_t** plan);
 /* Number of replicas and the B+1 atom offsets (may be NULL). */
 int mls6_batch_size(const mls6_batch_t* b, int* B, int64_t* offsets);
 
+/* Execution mode.  persistent = 1: when every replica is FP32
+ * with at least two levels, the shared-memory stencil kernel and 1..8 pair
+ * lanes per atom, the graph holds one persistent kernel: its blocks take
+ * (stage, replica, block) work items from a device queue in stage-major
+ * order (replicas in decreasing cost within a stage), wait until the
+ * replica's previous stage has counted all its blocks (bounded waits, see
+ * mls6_batch_set_wait), run the same kernel body as the per-stage launch,
+ * and count the item done.  Results equal mls6_eval's on each replica's
+ * plan bit for bit.  persistent = 0 (default), or an ineligible batch: the
+ * graph of per-replica kernel chains described above.  Waits for the
+ * batch's work; the next evaluation re-captures. */
+int mls6_batch_set_mode(mls6_batch_t* b, int persistent);
+
+/* 1 if the batch's graph runs (or, before its next capture, will run) the
+ * persistent kernel, 0 otherwise. */
+int mls6_batch_mode(const mls6_batch_t* b);
+
+/* Bounded waits of the persistent kernel: a block polls a replica's stage
+ * counter at most `limit` times (about 0.1 us apart; default 2^22, i.e. well
+ * under a second) before it records a timeout and every block leaves the
+ * kernel; the call then reports MLS6_ERR_TIMEOUT (host energy pointers, or
+ * mls6_batch_last_error).  withhold >= 0 is a test hook: the item with that
+ * number never counts as done, so the waits behind it run out (no fault, no
+ * trap: the kernel returns).  -1 disables it.  Takes effect at the next
+ * evaluation. */
+int mls6_batch_set_wait(mls6_batch_t* b, long long limit, long long withhold);
+
+/* Waits for the batch's work and returns MLS6_ERR_TIMEOUT if the persistent
+ * kernel's bounded wait ran out, MLS6_ERR_NONFINITE if a replica saw a
+ * non-finite input, else MLS6_OK. */
+int mls6_batch_last_error(mls6_batch_t* b);
+
 /* Release the batch, its plans and all their device memory.  NULL is ignored. */
 void mls6_batch_destroy(mls6_batch_t* b);
 
@@ -368,8 +420,12 @@ void mls6_batch_destroy(mls6_batch_t* b);
  * layers, BF16 weights and activations on the tensor cores with FP32
  * accumulation.  Parameters: one FP32 vector of mls6_mlp_n_params() values,
  * W1 (128 x 64, row = input) b1 W2 (64 x 64) b2 W3 b3 W4 (64 x 8) b4.
- * Training: loss (1/N) sum_i sum_{c<3} (y_ic - t_ic)^2, FP32 gradient with
- * fixed-order reductions (reproducible), Adam (0.9, 0.999, 1e-8).
+ * Training: loss (1/N) sum_i sum_{c<3} (y_ic - t_ic)^2; the backward pass
+ * runs on the tensor cores in BF16 with FP32 accumulation (activation
+ * gradients dZ = (dZ' W^T)(1 - h^2) kept in BF16, weight gradients X^T dZ
+ * and H^T dZ, bias gradients as products with a ones operand), partial sums
+ * over blocks of atoms reduced in a fixed order (reproducible bit for bit);
+ * Adam (0.9, 0.999, 1e-8) on FP32 master weights.
  * All calls are asynchronous on the model's stream (mls6_mlp_set_stream)
  * except where a host result is returned; calls that take a plan run on the
  * plan's stream.
@@ -401,11 +457,13 @@ int mls6_mlp_forward(mls6_mlp_t* m, const void* X, int64_t N, float* Y);
 
 /* Gradient of the loss for targets T (device, N x 3 floats) into grad
  * (device, n_params floats; may be NULL) and the loss (host, may be NULL:
- * a host loss makes the call wait). */
+ * a host loss makes the call wait).  X (N x 128 bf16) must be 16-byte
+ * aligned (its rows are copied in 16-byte pieces); MLS6_ERR_ARG otherwise. */
 int mls6_mlp_grad(mls6_mlp_t* m, const void* X, const float* T, int64_t N, float* grad,
                   double* loss);
 
-/* One Adam step on the batch (X, T) with learning rate lr. */
+/* One Adam step on the batch (X, T) with learning rate lr (X aligned as
+ * for mls6_mlp_grad). */
 int mls6_mlp_train_step(mls6_mlp_t* m, const void* X, const float* T, int64_t N, float lr,
                         double* loss);
 

@@ -24,7 +24,7 @@
  *     windowed-out remainder (compensated summation over the images).
  *  R8 virial: strain derivative with grids deforming with the cell.
  *  R9 cutoff tests are strict (r < cutoff); g_k is exactly 0 beyond.
- *  R10 interpolation order p = 5 uses the C^1 quintic below (the paper
+ *  R18 interpolation order p = 5 uses the C^1 quintic below (the paper
  *     compares p = 5 but prints only the cubic); parity unpinned against
  *     the paper for p = 5: it is pinned to its defining conditions.
  */
@@ -62,8 +62,8 @@ int orc_get_threads(void) {
  *     gamma_n(rho) = sum_{k=0..n} binom(-1/2, k) (rho^12 - 1)^k   (rho < 1),
  * which matches rho^-6 and its first n derivatives at rho = 1.  n = 2 is
  * Eq. (gamma): 15/8 - 5/4 rho^12 + 3/8 rho^24.  The other n (Sec. III.B
- * compares C^1 .. C^4) follow the same construction, a reading of the
- * paper, which prints only n = 2. */
+ * compares C^1 .. C^4) follow the same construction (reading R17 of the
+ * paper, which prints only n = 2). */
 static int g_smooth = 2;
 
 void orc_set_smoothing(int n) { g_smooth = (n >= 1 && n <= 4) ? n : 2; }
@@ -131,7 +131,7 @@ double orc_dgk(int k, int l, double a, double r) {
  * Phi(+-2) = 0), C^1, and reproducing polynomials of degree <= 4 (order 5).
  * Those conditions leave one free coefficient; the member taken is the one
  * whose outer piece is a product of linear factors (roots 1, 2, 3, 3, 4),
- * i.e. (reading R10)
+ * i.e. (reading R18)
  *   |t| <= 1:  (1 - t^2)(2 - t)(6 + 3t - 5t^2) / 12
  *   1..2:      (t - 1)(t - 2)(t - 3)(5t^2 - 9t - 4) / 24
  *   2..3:     -(t - 1)(t - 2)(t - 3)^2 (t - 4) / 24       (t = |t| here). */

@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mls6_plan.cpp", "mls6_eval.cu", "mls6_bin.cu", "mls6_pair.cu", "mls6_grid.cu",
            "mls6_noalloc.cu", "mls6_batch.cu", "mls6_stencil_tc.cu",
-           "mls6_learn.cu", "mls6_peaks.cu", "mls6_stencil_mma.cu"]
+           "mls6_learn.cu", "mls6_peaks.cu", "mls6_stencil_mma.cu", "mls6_persist.cu"]
 
 
 def _nvcc() -> str:

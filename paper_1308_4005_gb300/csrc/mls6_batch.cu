@@ -1,6 +1,12 @@
 // Batches of independent replicas (systems of uneven size, each its own box
 // and grid hierarchy) evaluated by one CUDA graph launch.
 //
+// FP32 batches can run one persistent kernel inside that graph instead
+// (mls6_batch_set_mode(b, 1)): a device work queue of (stage, replica, block)
+// items with bounded waits (mls6_persist.cu).  By default, and whenever the
+// autotuner measures it faster, the graph holds every replica's kernel
+// chain:
+//
 // Every replica is a complete plan (its own workspace and tables); the batch
 // captures all their kernel sequences into a single graph whose replicas are
 // spread over K independent chains ("branches"), so that kernels of small
@@ -46,6 +52,11 @@ struct Batch {
   double* h_ew = nullptr;         // pinned: 7 per replica + flags
   cudaGraphExec_t gexec = nullptr;
   int launches = 0;               // kernels in the captured graph
+  int mode = 0;                   // 1: one persistent kernel where eligible, 0: kernel chains
+  bool persistent = false;        // the captured graph runs the persistent kernel
+  PersistExec* px = nullptr;      // its work queue (rebuilt with the graph)
+  long long wait_limit = 1LL << 22, withhold = -1;  // bounded waits, test hook
+  int* h_err = nullptr;           // pinned: the queue's error word
   struct Key {
     const void *pos, *c, *forces;
     bool vir;
@@ -97,6 +108,8 @@ static void lpt(int B, const double* cost, int K, int* branch_of, double* load) 
 static void free_batch(Batch* b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  persist_free(b->px);
+  if (b->h_err) cudaFreeHost(b->h_err);
   for (Plan* p : b->plans)
     if (p) mls6_destroy(reinterpret_cast<mls6_plan_t*>(p));
   if (b->d_ew) cudaFree(b->d_ew);
@@ -121,6 +134,11 @@ static void reset_graph(Batch* b) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
   }
+  if (b->px) {
+    persist_free(b->px);
+    b->px = nullptr;
+  }
+  b->persistent = false;
 }
 
 static void assign(Batch* b) {
@@ -131,8 +149,55 @@ static void assign(Batch* b) {
 // Capture every replica into one graph: K chains from a common root, each
 // replica ordered after the previous one of its chain, all chains joined
 // before the flag gather.
+// The persistent form: one graph of two small resets and one kernel that
+// runs every replica's stages from a device work queue (mls6_persist.cu).
+static int capture_persistent(Batch* b, const void* pos, const void* c, void* forces, bool vir) {
+  // the persistent kernel's blocks have 256 threads: two stencil thread
+  // groups per tile; the replicas' plans take that shape too, so that each
+  // still equals its own plan bit for bit
+  for (Plan* p : b->plans) {
+    const int rc = mls6_set_tuning(reinterpret_cast<mls6_plan_t*>(p), 0, 2);
+    if (rc) return rc;
+  }
+  PersistExec* x = nullptr;
+  int rc = persist_build(&x, b->plans.data(), b->B, b->off.data(), b->cost.data(), pos, c,
+                         forces, b->d_ew, b->d_flags, vir);
+  if (rc) return rc;
+  persist_set_wait(x, b->wait_limit, b->withhold);
+  CK(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+  const int nl = persist_launch(x, b->s0);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->s0, &graph);
+  if (nl < 0 || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    persist_free(x);
+    return nl < 0 ? nl : MLS6_ERR_CUDA;
+  }
+  ce = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    b->gexec = nullptr;
+    persist_free(x);
+    return MLS6_ERR_CUDA;
+  }
+  b->px = x;
+  b->persistent = true;
+  b->key = {pos, c, forces, vir};
+  b->launches = nl;
+  return MLS6_OK;
+}
+
+static bool persistent_ok(const Batch* b) {
+  if (b->mode != 1 || b->prec != MLS6_FP32) return false;
+  for (const Plan* p : b->plans)
+    if (!persist_eligible(p)) return false;
+  return true;
+}
+
 static int capture(Batch* b, const void* pos, const void* c, void* forces, bool vir) {
   reset_graph(b);
+  if (persistent_ok(b)) return capture_persistent(b, pos, c, forces, vir);
   const size_t e = b->elem();
   const int K = b->branches;
   std::vector<cudaEvent_t> tail(K, b->ev_root);
@@ -229,6 +294,9 @@ static int eval(Batch* b, const void* pos, const void* c, void* forces, double* 
     CK(cudaMemcpyAsync(b->h_ew, b->d_ew, 7 * sizeof(double) * B, cudaMemcpyDeviceToHost, b->s0));
     CK(cudaMemcpyAsync(b->h_ew + 7 * B, b->d_flags, sizeof(int) * B, cudaMemcpyDeviceToHost,
                        b->s0));
+    if (b->persistent)
+      CK(cudaMemcpyAsync(b->h_err, persist_error_word(b->px), sizeof(int),
+                         cudaMemcpyDeviceToHost, b->s0));
   }
   if (energy && is_dev(energy))
     CK(cudaMemcpy2DAsync(energy, sizeof(double), b->d_ew, 7 * sizeof(double), sizeof(double), B,
@@ -245,6 +313,7 @@ static int eval(Batch* b, const void* pos, const void* c, void* forces, double* 
       if (virial && !is_dev(virial))
         for (int k = 0; k < 6; ++k) virial[6 * r + k] = b->h_ew[7 * r + 1 + k];
     }
+    if (b->persistent && *b->h_err) return MLS6_ERR_TIMEOUT;
     const int* fl = reinterpret_cast<const int*>(b->h_ew + 7 * B);
     for (size_t r = 0; r < B; ++r)
       if (fl[r]) return flag_status(fl[r]);
@@ -328,6 +397,9 @@ int mls6_batch_plan(mls6_batch_t** out, int B, const double* boxes, const int64_
     rc = mls6_plan(&p, boxes + 3 * r, N[r], a, h, levels, order, precision);
     if (rc) break;
     b->plans[r] = reinterpret_cast<Plan*>(p);
+    // replicas keep the per-atom pair forms (the persistent kernel runs
+    // those; the cluster form is for single large systems)
+    b->plans[r]->pair_split = pair_split_atom(b->plans[r]);
     rc = plan_streams(b->plans[r]);
     b->off[r + 1] = b->off[r] + N[r];
     double hh = b->plans[r]->lv[1].h[0];
@@ -344,7 +416,8 @@ int mls6_batch_plan(mls6_batch_t** out, int B, const double* boxes, const int64_
     if (cudaMalloc((void**)&b->d_ew, 7 * sizeof(double) * B) != cudaSuccess ||
         cudaMalloc((void**)&b->d_flags, sizeof(int) * B) != cudaSuccess ||
         cudaMalloc((void**)&b->d_flag_src, sizeof(int*) * B) != cudaSuccess ||
-        cudaMallocHost((void**)&b->h_ew, (7 * sizeof(double) + sizeof(int)) * B) != cudaSuccess)
+        cudaMallocHost((void**)&b->h_ew, (7 * sizeof(double) + sizeof(int)) * B) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_err, sizeof(int)) != cudaSuccess)
       rc = MLS6_ERR_NOMEM;
   }
   if (rc == MLS6_OK) {
@@ -419,15 +492,15 @@ int mls6_batch_info(const mls6_batch_t* batch, int* branches, int* split, int* g
   return MLS6_OK;
 }
 
-int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* forces, int reps,
-                    double* best_sec) {
-  if (!batch || reps < 1) return MLS6_ERR_ARG;
-  Batch* b = reinterpret_cast<Batch*>(batch);
-  if (b->off[b->B] > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+// Tune the batch's current launch form (branch count and kernel shapes of
+// the chains, or the pair lanes of the persistent kernel); leaves the best
+// configuration applied and its time in *best_out.
+static int tune_form(Batch* b, const void* pos, const void* c, void* forces, int reps,
+                     double* best_out) {
   // seed shapes: each plan's heuristic value
   std::vector<int> s0(b->B), g0(b->B);
   for (int r = 0; r < b->B; ++r) {
-    s0[r] = pair_split(b->plans[r]);
+    s0[r] = pair_split_atom(b->plans[r]);
     g0[r] = b->plans[r]->stencil_groups;
   }
   auto shaped = [&](int sb, int gb, std::vector<int>& s, std::vector<int>& g) {
@@ -435,7 +508,9 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
     g.resize(b->B);
     for (int r = 0; r < b->B; ++r) {
       int x = sb >= 0 ? s0[r] << sb : s0[r] >> -sb;
-      s[r] = std::max(1, std::min(pair_cluster_ok(b->plans[r]) ? kPairSplitMax : 8, x));
+      // the persistent kernel runs the per-atom pair kernel (1..8 lanes)
+      const int smax = (b->mode == 1 || !pair_cluster_ok(b->plans[r])) ? 8 : kPairSplitMax;
+      s[r] = std::max(1, std::min(smax, x));
       int y = gb >= 0 ? g0[r] << gb : g0[r] >> -gb;
       g[r] = std::max(1, std::min(4, y));
     }
@@ -448,9 +523,13 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
   double best = 0.0;
   rc = time_batch(b, pos, c, forces, reps, &best);
   if (rc) return rc;
+  // the persistent kernel has no chains and fixed stencil groups: tune the
+  // pair lanes only
+  const bool pers = b->persistent;
   // 1. branch count
   const int Ks[] = {1, 2, 4, 8, 16, 32, 64};
   for (int K : Ks) {
+    if (pers) break;
     if (K > b->B || K == best_k) continue;
     b->branches = K;
     assign(b);
@@ -466,7 +545,7 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
   b->branches = best_k;
   assign(b);
   // 2. pair lanes, 3. stencil groups: one power of two either way
-  for (int pass = 0; pass < 2; ++pass)
+  for (int pass = 0; pass < (pers ? 1 : 2); ++pass)
     for (int d : {-1, 1}) {
       const int sb = pass == 0 ? best_sb + d : best_sb, gb = pass == 1 ? best_gb + d : best_gb;
       shaped(sb, gb, s, g);
@@ -484,7 +563,49 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
   shaped(best_sb, best_gb, s, g);
   rc = apply_shapes(b, s, g);
   if (rc) return rc;
-  if (best_sec) *best_sec = best;
+  *best_out = best;
+  return MLS6_OK;
+}
+
+int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* forces, int reps,
+                    double* best_sec) {
+  if (!batch || reps < 1) return MLS6_ERR_ARG;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (b->off[b->B] > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+  double t0 = 0.0;
+  int rc = tune_form(b, pos, c, forces, reps, &t0);
+  if (rc) return rc;
+  // FP32 batches whose plans the persistent kernel can run: tune the other
+  // launch form too and keep the faster
+  // (the persistent form is tuned with 1..8 lanes per atom, which it runs)
+  bool other = b->prec == MLS6_FP32;
+  for (const Plan* p : b->plans)
+    other = other && p->N > 0 && p->levels >= 2 && !p->stencil_global && !p->stencil_mma &&
+            !p->stencil_tc && p->sm.n == 2 && p->order == 3;
+  if (other) {
+    const int m0 = b->mode, k0 = b->branches;
+    std::vector<int> s0(b->B), g0(b->B);
+    for (int r = 0; r < b->B; ++r) {
+      s0[r] = b->plans[r]->pair_split;
+      g0[r] = b->plans[r]->stencil_groups;
+    }
+    b->mode = 1 - m0;
+    reset_graph(b);
+    double t1 = 0.0;
+    rc = tune_form(b, pos, c, forces, reps, &t1);
+    if (rc) return rc;
+    if (t1 < t0) {
+      t0 = t1;
+    } else {  // back to the first form and its shapes
+      b->mode = m0;
+      b->branches = k0;
+      assign(b);
+      rc = apply_shapes(b, s0, g0);
+      if (rc) return rc;
+      reset_graph(b);
+    }
+  }
+  if (best_sec) *best_sec = t0;
   return MLS6_OK;
 }
 
@@ -502,6 +623,52 @@ int mls6_batch_replica(mls6_batch_t* batch, int r, mls6_plan_t** plan) {
   Batch* b = reinterpret_cast<Batch*>(batch);
   if (r < 0 || r >= b->B) return MLS6_ERR_ARG;
   *plan = reinterpret_cast<mls6_plan_t*>(b->plans[r]);
+  return MLS6_OK;
+}
+
+int mls6_batch_set_mode(mls6_batch_t* batch, int persistent) {
+  if (!batch || persistent < 0 || persistent > 1) return MLS6_ERR_ARG;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (b->s0 && cudaStreamSynchronize(b->s0) != cudaSuccess) return MLS6_ERR_CUDA;
+  b->mode = persistent;
+  reset_graph(b);
+  return MLS6_OK;
+}
+
+int mls6_batch_mode(const mls6_batch_t* batch) {
+  if (!batch) return MLS6_ERR_ARG;
+  const Batch* b = reinterpret_cast<const Batch*>(batch);
+  // the captured graph's form, or the form the next evaluation captures
+  return (b->gexec ? b->persistent : persistent_ok(b)) ? 1 : 0;
+}
+
+int mls6_batch_set_wait(mls6_batch_t* batch, long long limit, long long withhold) {
+  if (!batch || limit < 1) return MLS6_ERR_ARG;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (b->s0 && cudaStreamSynchronize(b->s0) != cudaSuccess) return MLS6_ERR_CUDA;
+  b->wait_limit = limit;
+  b->withhold = withhold;
+  reset_graph(b);
+  return MLS6_OK;
+}
+
+int mls6_batch_last_error(mls6_batch_t* batch) {
+  if (!batch) return MLS6_ERR_ARG;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (b->s0 && cudaStreamSynchronize(b->s0) != cudaSuccess) return MLS6_ERR_CUDA;
+  if (b->persistent) {
+    int e = 0;
+    if (cudaMemcpy(&e, persist_error_word(b->px), sizeof(int), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return MLS6_ERR_CUDA;
+    if (e) return MLS6_ERR_TIMEOUT;
+  }
+  std::vector<int> fl(b->B, 0);
+  if (cudaMemcpy(fl.data(), b->d_flags, sizeof(int) * b->B, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return MLS6_ERR_CUDA;
+  for (int f : fl)
+    if (f) return flag_status(f);
   return MLS6_OK;
 }
 

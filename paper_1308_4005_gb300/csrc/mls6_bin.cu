@@ -9,7 +9,6 @@
 
 namespace mls6 {
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 template <typename T> struct BinArgs {
   Box3<T> box;
@@ -24,7 +23,7 @@ template <typename T> struct BinArgs {
 // kScanTile cells to tsum (a shared-memory histogram first, then one
 // integer atomic per touched tile).
 template <typename T>
-__global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
+__device__ __forceinline__ void k_bin_body(const Blk bk,const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
                       BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
                       int* __restrict__ count, int* __restrict__ flag, int* __restrict__ tsum,
                       int ntiles) {
@@ -32,7 +31,7 @@ __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int s
   pos += z; cc += z;
   __shared__ T wmax[32];
   __shared__ int hist[kScanDirect];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bk.x * blockDim.x + threadIdx.x;
   if (tsum)
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
@@ -77,11 +76,19 @@ __global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int s
       if (hist[t]) atomicAdd(&tsum[t], hist[t]);
 }
 
+template <typename T>
+__global__ void k_bin(const T* __restrict__ pos, const T* __restrict__ cc, int stride, int N,
+                      BinArgs<T> g, Vec4<T>* __restrict__ posw, int* __restrict__ cell_of,
+                      int* __restrict__ count, int* __restrict__ flag, int* __restrict__ tsum,
+                      int ntiles) {
+  k_bin_body<T>(Blk::self(), pos, cc, stride, N, g, posw, cell_of, count, flag, tsum, ntiles);
+}
+
 // Tile pass, for more than kScanDirect tiles: per-tile sums of the cell
 // counts; the last block to finish (ticket counter, reset by that block)
 // turns them into exclusive tile offsets (block-wide scan, blockDim.x tiles
 // at a time with a running carry) and writes the grand total to start[n].
-__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
+__device__ __forceinline__ void k_scan_tiles_body(const Blk bk,const int* __restrict__ count, long n, int* __restrict__ tsum,
                              int* __restrict__ start, int* __restrict__ flag) {
   const long z = pdl_begin();
   count += z;
@@ -89,7 +96,7 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
   __shared__ bool last;
   unsigned* ticket = reinterpret_cast<unsigned*>(flag + 2);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long base = (long)blockIdx.x * kScanTile;
+  const long base = (long)bk.x * kScanTile;
   int s = 0;
   for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
     if (base + t < n) s += count[base + t];
@@ -99,17 +106,17 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
   if (threadIdx.x == 0) {
     int tot = 0;
     for (int w = 0; w < nw; ++w) tot += shm[w];
-    tsum[blockIdx.x] = tot;
+    tsum[bk.x] = tot;
     __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(ticket, 1u) == bk.n - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   int carry = 0;
-  for (int t0 = 0; t0 < (int)gridDim.x; t0 += blockDim.x) {
+  for (int t0 = 0; t0 < (int)bk.n; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
-    const int v = t < (int)gridDim.x ? ((volatile int*)tsum)[t] : 0;
+    const int v = t < (int)bk.n ? ((volatile int*)tsum)[t] : 0;
     int incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       const int u = __shfl_up_sync(0xffffffffu, incl, o);
@@ -124,7 +131,7 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
       if (w < wid) wbase += ws;
       total += ws;
     }
-    if (t < (int)gridDim.x) tsum[t] = carry + wbase + incl - v;
+    if (t < (int)bk.n) tsum[t] = carry + wbase + incl - v;
     carry += total;
   }
   if (threadIdx.x == 0) {
@@ -133,6 +140,16 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
   }
 }
 
+#ifndef MLS6_DEVICE_ONLY  // non-template kernel, left out where another unit includes this file
+__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
+                             int* __restrict__ start, int* __restrict__ flag) {
+  k_scan_tiles_body(Blk::self(), count, n, tsum, start, flag);
+}
+#else
+__global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restrict__ tsum,
+                             int* __restrict__ start, int* __restrict__ flag);
+#endif  // MLS6_DEVICE_ONLY
+
 // Scan inside each tile (256 threads x 8 consecutive cells), write start[],
 // reset count[] for use as fill counters by the scatter, and keep the
 // largest cell population in flag[3] (one atomic maximum per block).  The
@@ -140,7 +157,7 @@ __global__ void k_scan_tiles(const int* __restrict__ count, long n, int* __restr
 // kScanDirect tiles, tsum holding the tile sums from the binning) the sum of
 // the preceding tiles' sums, formed by each block; the last tile then also
 // writes the grand total to start[n].
-__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ tsum,
+__device__ __forceinline__ void k_scan_final_body(const Blk bk,int* __restrict__ count, long n, const int* __restrict__ tsum,
                              int* __restrict__ start, int direct, int* __restrict__ flag) {
   const long z = pdl_begin();
   tsum += z;
@@ -148,7 +165,7 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
   __shared__ int toff;
   constexpr int PER = kScanTile / 256;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * PER;
+  long base = (long)bk.x * kScanTile + (long)threadIdx.x * PER;
   int v[PER], s = 0, mx = 0;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
@@ -158,7 +175,7 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
   }
   int pre = 0;  // direct: this thread's share of the preceding tiles' sums
   if (direct)
-    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) pre += tsum[t];
+    for (int t = threadIdx.x; t < (int)bk.x; t += blockDim.x) pre += tsum[t];
   for (int o = 16; o > 0; o >>= 1) {
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     pre += __shfl_xor_sync(0xffffffffu, pre, o);
@@ -174,7 +191,7 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int w = 0; w < nw; ++w) acc += wmx[w];
-    toff = direct ? acc : tsum[blockIdx.x];
+    toff = direct ? acc : tsum[bk.x];
   }
   if (wid == 0) {
     int x = lane < nw ? wsum[lane] : 0;
@@ -195,7 +212,7 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
     }
     excl += v[k];
   }
-  if (direct && threadIdx.x == blockDim.x - 1 && blockIdx.x == gridDim.x - 1) start[n] = excl;
+  if (direct && threadIdx.x == blockDim.x - 1 && bk.x == bk.n - 1) start[n] = excl;
   __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
@@ -204,18 +221,35 @@ __global__ void k_scan_final(int* __restrict__ count, long n, const int* __restr
   }
 }
 
+#ifndef MLS6_DEVICE_ONLY  // non-template kernel, left out where another unit includes this file
+__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ tsum,
+                             int* __restrict__ start, int direct, int* __restrict__ flag) {
+  k_scan_final_body(Blk::self(), count, n, tsum, start, direct, flag);
+}
+#else
+__global__ void k_scan_final(int* __restrict__ count, long n, const int* __restrict__ tsum,
+                             int* __restrict__ start, int direct, int* __restrict__ flag);
+#endif  // MLS6_DEVICE_ONLY
+
 template <typename T>
-__global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
+__device__ __forceinline__ void k_scatter_body(const Blk bk,const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
                           const int* __restrict__ start, int* __restrict__ fill,
                           Vec4<T>* __restrict__ sorted, int* __restrict__ sidx) {
   const long z = pdl_begin();
   posw += z; cell_of += z; start += z;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = bk.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int cell = cell_of[i];
   int slot = start[cell] + atomicAdd(&fill[cell], 1);
   sorted[slot] = posw[i];
   sidx[slot] = i;
+}
+
+template <typename T>
+__global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restrict__ cell_of, int N,
+                          const int* __restrict__ start, int* __restrict__ fill,
+                          Vec4<T>* __restrict__ sorted, int* __restrict__ sidx) {
+  k_scatter_body<T>(Blk::self(), posw, cell_of, N, start, fill, sorted, sidx);
 }
 
 // Each cell's records sorted by input index, so that every later sum runs
@@ -227,12 +261,12 @@ __global__ void k_scatter(const Vec4<T>* __restrict__ posw, const int* __restric
 // bitwise reproducibility is lost for them).  Also returns the cell's
 // counter, and the first nreset tile sums, to zero for the next binning.
 template <typename T>
-__global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
+__device__ __forceinline__ void k_cellsort_body(const Blk bk,const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
                            int* __restrict__ sidx, int* __restrict__ count,
                            int* __restrict__ tsum, int nreset) {
   const long z = pdl_begin();
   start += z;
-  long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long cell = (long)bk.x * blockDim.x + threadIdx.x;
   if (cell < nreset) tsum[cell] = 0;
   if (cell >= ncell) return;
   count[cell] = 0;
@@ -284,8 +318,15 @@ __global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* _
   }
 }
 
-template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStream_t st) {
-  const int N = (int)p->N;
+template <typename T>
+__global__ void k_cellsort(const int* __restrict__ start, long ncell, Vec4<T>* __restrict__ sorted,
+                           int* __restrict__ sidx, int* __restrict__ count,
+                           int* __restrict__ tsum, int nreset) {
+  k_cellsort_body<T>(Blk::self(), start, ncell, sorted, sidx, count, tsum, nreset);
+}
+
+// Arguments of the binning kernel for a plan.
+template <typename T> static BinArgs<T> bin_args(const Plan* p) {
   BinArgs<T> bg;
   for (int d = 0; d < 3; ++d) {
     bg.box.L[d] = (T)p->L[d];
@@ -293,6 +334,12 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
     bg.inv_w[d] = (T)p->cg.inv_w[d];
     bg.nc[d] = p->cg.nc[d];
   }
+  return bg;
+}
+
+template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStream_t st) {
+  const int N = (int)p->N;
+  const BinArgs<T> bg = bin_args<T>(p);
   const long ncell = p->cg.ncell;
   const long ntiles = cdiv(ncell, kScanTile);
   // direct: tile sums from the binning (kept zero between binnings by the
@@ -317,7 +364,9 @@ template <typename T> int launch_bin(Plan* p, const T* pos, const T* cc, cudaStr
   return direct ? 4 : 5;
 }
 
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 template int launch_bin<float>(Plan*, const float*, const float*, cudaStream_t);
 template int launch_bin<double>(Plan*, const double*, const double*, cudaStream_t);
 
+#endif  // MLS6_DEVICE_ONLY
 }  // namespace mls6

@@ -7,6 +7,14 @@
 
 namespace mls6 {
 
+// Block coordinates of a kernel body: the hardware block index and grid
+// size in a kernel of its own, a work item's block index and block count
+// when a persistent kernel runs the body.
+struct Blk {
+  unsigned x, n;
+  static __device__ __forceinline__ Blk self() { return Blk{blockIdx.x, gridDim.x}; }
+};
+
 template <typename T> struct Box3 {
   T L[3], invL[3];
 };
@@ -43,6 +51,62 @@ template <typename T> __device__ __forceinline__ void phi4(T t, T w[4], T dw[4])
   dw[1] = t * (T(-5) + T(4.5) * t);
   dw[2] = s * (T(5) - T(4.5) * s);
   dw[3] = T(-0.5) * t * (T(2) - T(3) * t);
+}
+
+// Order p = 5: the C^1 quintic (even, support |t| < 3, reproducing
+// polynomials of degree <= 4; the member whose outer piece continues to a
+// root at |t| = 4).  Weights of the six nodes base-2 .. base+3 of an atom at
+// offset t in [0,1) from node base -- Phi(2+t), Phi(1+t), Phi(t), Phi(1-t),
+// Phi(2-t), Phi(3-t) -- in factored form (no cancellation near the ends of
+// the support), and (phi6 only) their derivatives in t.
+template <typename T> __device__ __forceinline__ void phi6w(T t, T w[6]) {
+  const T s = T(1) - t, tp = T(1) + t, tm = T(2) - t;
+  const T k24 = T(1.0 / 24.0), k12 = T(1.0 / 12.0);
+  w[0] = k24 * t * s * s * tp * tm;
+  w[1] = k24 * t * s * tm * (T(5) * t * t + t - T(8));
+  w[2] = k12 * s * tm * tp * (T(6) + T(3) * t - T(5) * t * t);
+  w[3] = k12 * t * tm * tp * (T(4) + T(7) * t - T(5) * t * t);
+  w[4] = k24 * t * s * tp * (T(5) * t * t - T(11) * t - T(2));
+  w[5] = k24 * t * t * s * tm * tp;
+}
+
+template <typename T> __device__ __forceinline__ void phi6(T t, T w[6], T dw[6]) {
+  phi6w(t, w);
+  const T s = T(1) - t;
+  const T k24 = T(1.0 / 24.0), k12 = T(1.0 / 12.0);
+  dw[0] = k24 * s * (((T(5) * t - T(7)) * t - T(4)) * t + T(2));
+  dw[1] = k24 * ((((T(25) * t - T(56)) * t - T(3)) * t + T(52)) * t - T(16));
+  dw[2] = -k12 * t * (((T(25) * t - T(52)) * t - T(15)) * t + T(50));
+  dw[3] = -k12 * s * (((T(25) * t - T(23)) * t - T(44)) * t - T(8));
+  dw[4] = -k24 * ((((T(25) * t - T(44)) * t - T(21)) * t + T(22)) * t + T(2));
+  dw[5] = k24 * t * (((T(5) * t - T(8)) * t - T(3)) * t + T(4));
+}
+
+// Basis of NP = p + 1 nodes per axis: weights (and derivatives) of nodes
+// base - (NP/2 - 1) .. base + NP/2.
+template <int NP, typename T> __device__ __forceinline__ void phiw(T t, T* w) {
+  if constexpr (NP == 6)
+    phi6w(t, w);
+  else
+    phi4w(t, w);
+}
+template <int NP, typename T> __device__ __forceinline__ void phid(T t, T* w, T* dw) {
+  if constexpr (NP == 6)
+    phi6(t, w, dw);
+  else
+    phi4(t, w, dw);
+}
+
+// Restriction / prolongation: Phi at half-integers.  For a fine node at
+// coarse position c + 1/2 the NP coarse nodes c - (NP/2 - 1) .. c + NP/2
+// weigh Phi(NP/2 - 1/2), ..., Phi(1/2), Phi(1/2), ..., Phi(NP/2 - 1/2);
+// restriction takes the same values at fine offsets +-1, +-3, +-5 from 2 mu.
+template <int NP, typename T> __device__ __forceinline__ T half_weight(int k) {
+  // k = 0: Phi(1/2), 1: Phi(3/2), 2: Phi(5/2)
+  if constexpr (NP == 6)
+    return k == 0 ? T(150.0 / 256.0) : (k == 1 ? T(-25.0 / 256.0) : T(3.0 / 256.0));
+  else
+    return k == 0 ? T(0.5625) : T(-0.0625);
 }
 
 // Programmatic dependent launch: every kernel of the evaluation chain first

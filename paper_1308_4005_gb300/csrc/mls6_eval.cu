@@ -25,7 +25,6 @@ namespace mls6 {
     if (e_ != cudaSuccess) return MLS6_ERR_CUDA; \
   } while (0)
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // Fixed-order reduction of the energy and virial partials (one block).
 __global__ void k_reduce(const double* __restrict__ epart, long ne,

@@ -8,7 +8,6 @@
 
 namespace mls6 {
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------------ anterpolation
 
@@ -21,10 +20,16 @@ __device__ __forceinline__ double lb_coef_d(int k) {
 }
 
 // Fixed-point accumulation of the anterpolation: 32-bit integers for the
-// FP32 modes (sums kept below 2^30; resolution ~1e-6 of the largest possible
-// node sum, below FP32 rounding of the grid part), 64-bit for FP64 (below
-// 2^61; resolution ~1e-18 of it).  The conversions stay in the kernel's own
-// precision: FP64 arithmetic is slow on this GPU.
+// FP32 modes (sums kept below 2^30), 64-bit for FP64 (below 2^61).  Each
+// contribution is rounded to 2^(e-30) (FP32) or 2^(e-61) (FP64), where 2^e
+// exceeds the worst-case node sum B of fixed_exponent; B is a conservative
+// bound (most atoms in a cell x cells a support box meets x max |c|), so for
+// FP32 the step is ~1e-6 of a typical node sum of order 1: tens of FP32
+// rounding units per contribution, far below the FP32 path's force error
+// but not below FP32 rounding (the bound is tested against the FP64 oracle
+// on the 65,536-atom slab).  For FP64 it is ~1e-15 of a node sum.  The
+// conversions stay in the kernel's own precision: FP64 arithmetic is slow on
+// this GPU.
 template <typename T> struct Fixed;
 template <> struct Fixed<float> {
   using I = int;
@@ -67,23 +72,22 @@ __device__ __forceinline__ int fixed_exponent(const int* __restrict__ flag, doub
   return min(max(Fixed<T>::kBits - e, -120), 120);
 }
 
-// Eq. (anterpolation): q^1_mu += c_j phi_mu(x_j) over the 4x4x4 nodes of
-// every atom.  The contributions are rounded to the fixed-point grid 2^-s
-// and added as 64-bit integers: integer addition is associative, so the sums
-// (and everything downstream) do not depend on the order in which the
-// atomics land -- results are reproducible bit for bit.  The rounding
-// (relative 2^-s, s >= ~45 in practice) is far below FP64 parity needs.
+// Eq. (anterpolation): q^1_mu += c_j phi_mu(x_j) over the NP^3 nodes of
+// every atom (NP = p + 1: 4x4x4 for the cubic, 6x6x6 for the quintic).  The contributions are rounded to the fixed-point grid 2^-s
+// and added as integers (Fixed<T>): integer addition is associative, so the
+// sums (and everything downstream) do not depend on the order in which the
+// atomics land -- results are reproducible bit for bit.
 // A block of kBlock cell-sorted atoms touches a compact box of grid nodes:
 // when that box fits in shared memory the block first sums its
 // contributions there (integer atomics on shared memory) and then adds each
 // non-zero node once to the grid, which cuts the global atomics by the
-// overlap of the atoms' 4x4x4 supports; otherwise its atoms add to the grid
+// overlap of the atoms' supports; otherwise its atoms add to the grid
 // directly.  Both paths add the same integers, so the grid does not depend
 // on the path either.
 constexpr int kAnterpBoxBytes = 24 * 1024;
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_anterp(
+template <typename T, int NP = 4>
+__device__ __forceinline__ void k_anterp_body(const Blk bk,
     const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0, T ih1, T ih2,
     const int* __restrict__ flag, double span, typename Fixed<T>::U* __restrict__ qfx,
     const T* __restrict__ lbw, int lbm, double lbc) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
   sp += z;
   flag += z;
   lbw += z;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bk.x * blockDim.x + threadIdx.x;
   const bool valid = i < N;
   if (threadIdx.x < 3) {
     lo[threadIdx.x] = INT_MAX;
@@ -113,12 +117,12 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
   const int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
   __syncthreads();
   if (valid) {  // bounding box of the block's supports (unwrapped node indices)
-    atomicMin(&lo[0], b0 - 1);
-    atomicMin(&lo[1], b1 - 1);
-    atomicMin(&lo[2], b2 - 1);
-    atomicMax(&hi[0], b0 + 2);
-    atomicMax(&hi[1], b1 + 2);
-    atomicMax(&hi[2], b2 + 2);
+    atomicMin(&lo[0], b0 - (NP / 2 - 1));
+    atomicMin(&lo[1], b1 - (NP / 2 - 1));
+    atomicMin(&lo[2], b2 - (NP / 2 - 1));
+    atomicMax(&hi[0], b0 + NP / 2);
+    atomicMax(&hi[1], b1 + NP / 2);
+    atomicMax(&hi[2], b2 + NP / 2);
   }
   __syncthreads();
   const T scale = Fixed<T>::pow2(sexp);
@@ -129,38 +133,39 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
     for (int t = threadIdx.x; t < (int)vol; t += blockDim.x) box[t] = 0;
   __syncthreads();
   if (valid) {
-    T wx[4], wy[4], wz[4];
-    phi4w(u0 - f0, wx);
-    phi4w(u1 - f1, wy);
-    phi4w(u2 - f2, wz);
+    constexpr int B0 = NP / 2 - 1;  // first node of the support below base
+    T wx[NP], wy[NP], wz[NP];
+    phiw<NP>(u0 - f0, wx);
+    phiw<NP>(u1 - f1, wy);
+    phiw<NP>(u2 - f2, wz);
     if (in_box) {
-      const int x0 = b0 - 1 - lo[0], y0 = b1 - 1 - lo[1], z0 = b2 - 1 - lo[2];
+      const int x0 = b0 - B0 - lo[0], y0 = b1 - B0 - lo[1], z0 = b2 - B0 - lo[2];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < NP; ++c)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < NP; ++b) {
           const T wyz = p.w * wy[b] * wz[c];
           const int row = e0 * ((y0 + b) + e1 * (z0 + c)) + x0;
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < NP; ++a)
             atomicAdd(&box[row + a], (U)Fixed<T>::to_fixed(wyz * wx[a], scale));
         }
     } else {
-      int ix[4], iy[4], iz[4];
+      int ix[NP], iy[NP], iz[NP];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        ix[k] = wrapi(b0 - 1 + k, n0);
-        iy[k] = wrapi(b1 - 1 + k, n1);
-        iz[k] = wrapi(b2 - 1 + k, n2);
+      for (int k = 0; k < NP; ++k) {
+        ix[k] = wrapi(b0 - B0 + k, n0);
+        iy[k] = wrapi(b1 - B0 + k, n1);
+        iz[k] = wrapi(b2 - B0 + k, n2);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < NP; ++c)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < NP; ++b) {
           const T wyz = p.w * wy[b] * wz[c];
           const long rowi = (long)n0 * (iy[b] + (long)n1 * iz[c]);
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < NP; ++a)
             atomicAdd(&qfx[rowi + ix[a]], (U)Fixed<T>::to_fixed(wyz * wx[a], scale));
         }
     }
@@ -184,9 +189,17 @@ __global__ void __launch_bounds__(kBlock) k_anterp(
   }
 }
 
+template <typename T, int NP>
+__global__ void __launch_bounds__(kBlock) k_anterp(
+    const Vec4<T>* __restrict__ sp, int N, int n0, int n1, int n2, T ih0, T ih1, T ih2,
+    const int* __restrict__ flag, double span, typename Fixed<T>::U* __restrict__ qfx,
+    const T* __restrict__ lbw, int lbm, double lbc) {
+  k_anterp_body<T, NP>(Blk::self(), sp, N, n0, n1, n2, ih0, ih1, ih2, flag, span, qfx, lbw, lbm, lbc);
+}
+
 // q^1 = fixed-point sums * 2^-s in the plan's precision.
 template <typename T>
-__global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
+__device__ __forceinline__ void k_from_fixed_body(const Blk bk,const typename Fixed<T>::U* __restrict__ qfx, long np,
                              const int* __restrict__ flag, double span, T* __restrict__ q,
                              int lbm, double lbc) {
   __shared__ int sexp;
@@ -194,32 +207,42 @@ __global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long 
   qfx += z; flag += z;
   if (threadIdx.x == 0) sexp = fixed_exponent<T>(flag, span, lbm, lbc);
   __syncthreads();
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long i = (long)bk.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   q[i] = Fixed<T>::from_fixed((typename Fixed<T>::I)qfx[i], Fixed<T>::pow2(-sexp));
 }
 
-// Cells (with periodic images) that a box of width 4h can meet, product
-// over the axes.
+template <typename T>
+__global__ void k_from_fixed(const typename Fixed<T>::U* __restrict__ qfx, long np,
+                             const int* __restrict__ flag, double span, T* __restrict__ q,
+                             int lbm, double lbc) {
+  k_from_fixed_body<T>(Blk::self(), qfx, np, flag, span, q, lbm, lbc);
+}
+
+// Cells (with periodic images) that the support of one node's basis
+// function (width (p + 1) h) can meet, product over the axes.
 static double support_span(const Plan* p) {
   double s = 1.0;
-  for (int d = 0; d < 3; ++d) s *= std::ceil(4.0 * p->lv[1].h[d] / p->cg.w[d]) + 1.0;
+  const double width = p->order + 1.0;
+  for (int d = 0; d < 3; ++d) s *= std::ceil(width * p->lv[1].h[d] / p->cg.w[d]) + 1.0;
   return s;
 }
 
 // lbm >= 0: Lorentz-Berthelot channel m (coefficients computed from the
 // sorted sigma and sqrt(2 eps)); -1: the atoms' own coefficients.
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 double lb_coef(int m) {
   static const double binom[7] = {1, 6, 15, 20, 15, 6, 1};
   return m < 0 ? 0.0 : 0.125 * std::sqrt(binom[m]);
 }
+#endif  // MLS6_DEVICE_ONLY
 
 template <typename T> int launch_anterp(Plan* p, cudaStream_t st, int lbm) {
   const Level& L1 = p->lv[1];
   const int N = (int)p->N;
   const double span = support_span(p);
   const double lbc = lb_coef(lbm);
-  launch_pdl(k_anterp<T>, cdiv(N, kBlock), kBlock, 0, st, 
+  launch_pdl(p->order == 5 ? k_anterp<T, 6> : k_anterp<T, 4>, cdiv(N, kBlock), kBlock, 0, st,
       (const Vec4<T>*)p->d_sorted, N, L1.n[0], L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]),
       (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), p->d_flag, span,
       (typename Fixed<T>::U*)p->d_q1fx, (const T*)p->d_lbw, lbm, lbc);
@@ -266,37 +289,54 @@ template <typename T> int launch_lb_weights(Plan* p, const T* eps, cudaStream_t 
 // -------------------------------------------------------------- restriction
 
 // q^{k+1}_mu = sum_nu prod_d Phi(nu_d/2 - mu_d) q^k_nu; the nonzero weights
-// are Phi(0)=1, Phi(1/2)=9/16, Phi(3/2)=-1/16 at fine offsets 0, +-1, +-3
-// from 2 mu.
-template <typename T>
-__global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
+// are Phi(0)=1 at fine offset 0 from 2 mu and Phi(1/2), Phi(3/2) (and, for
+// the quintic, Phi(5/2)) at offsets +-1, +-3 (+-5): 9/16, -1/16 for the
+// cubic, 150/256, -25/256, 3/256 for the quintic.
+template <typename T, int NP = 4>
+__device__ __forceinline__ void k_restrict_body(const Blk bk,const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
                            int c0, int c1, int c2) {
   const long z = pdl_begin();
   qf += z;
-  long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long mu = (long)bk.x * blockDim.x + threadIdx.x;
   long np = (long)c0 * c1 * c2;
   if (mu >= np) return;
   int m0 = (int)(mu % c0), m1 = (int)((mu / c0) % c1), m2 = (int)(mu / ((long)c0 * c1));
-  const int off[5] = {-3, -1, 0, 1, 3};
-  const T wt[5] = {T(-0.0625), T(0.5625), T(1), T(0.5625), T(-0.0625)};
+  constexpr int NT = NP + 1, H = NP / 2;  // taps per axis, nonzero half-integer weights
+  int off[NT];
+  T wt[NT];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {  // offsets -(2H-1) .. -1 and 1 .. 2H-1
+    off[k] = -(2 * (H - 1 - k) + 1);
+    wt[k] = half_weight<NP, T>(H - 1 - k);
+    off[NT - 1 - k] = -off[k];
+    wt[NT - 1 - k] = wt[k];
+  }
+  off[H] = 0;
+  wt[H] = T(1);
   T acc = 0;
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < NT; ++c) {
     int z = wrapi(2 * m2 + off[c], f2);
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 0; b < NT; ++b) {
       int y = wrapi(2 * m1 + off[b], f1);
       long row = (long)f0 * (y + (long)f1 * z);
       T wyz = wt[b] * wt[c];
       T s = 0;
-      for (int a = 0; a < 5; ++a) s += wt[a] * qf[row + wrapi(2 * m0 + off[a], f0)];
+      for (int a = 0; a < NT; ++a) s += wt[a] * qf[row + wrapi(2 * m0 + off[a], f0)];
       acc += wyz * s;
     }
   }
   qc[mu] = acc;
 }
 
+template <typename T, int NP>
+__global__ void k_restrict(const T* __restrict__ qf, int f0, int f1, int f2, T* __restrict__ qc,
+                           int c0, int c1, int c2) {
+  k_restrict_body<T, NP>(Blk::self(), qf, f0, f1, f2, qc, c0, c1, c2);
+}
+
 template <typename T> int launch_restrict(Plan* p, int k, cudaStream_t st) {
   const Level &F = p->lv[k], &C = p->lv[k + 1];
-  launch_pdl(k_restrict<T>, cdiv(C.np, kBlock), kBlock, 0, st, (const T*)p->d_q[k], F.n[0], F.n[1],
+  launch_pdl(p->order == 5 ? k_restrict<T, 6> : k_restrict<T, 4>, cdiv(C.np, kBlock), kBlock, 0, st, (const T*)p->d_q[k], F.n[0], F.n[1],
                                                       F.n[2], (T*)p->d_q[k + 1], C.n[0], C.n[1],
                                                       C.n[2]);
   return 1;
@@ -353,14 +393,14 @@ inline void stencil_pitches(int S, int& Sx, int& Sp) {
 // G-th tap row (more resident warps for small grids); the groups' partial
 // outputs are added in shared memory, their virial terms in the block sum.
 template <typename T, bool VIR, int G>
-__global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> A,
+__device__ __forceinline__ void k_stencil_body(const Blk bk, const StencilArgs<T>& A,
                                                                  double* __restrict__ wpart) {
   pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 7];
   __shared__ T part[(G > 1 ? G - 1 : 1) * kStencilThreads * kStencilW];
-  if ((long)blockIdx.x >= A.sblocks) {  // coarsest level: one warp per node
-    const int mu = (int)((long)blockIdx.x - A.sblocks) * (int)(blockDim.x >> 5) +
+  if ((long)bk.x >= A.sblocks) {  // coarsest level: one warp per node
+    const int mu = (int)((long)bk.x - A.sblocks) * (int)(blockDim.x >> 5) +
                    (int)(threadIdx.x >> 5);
     if (mu < A.nt[0] * A.nt[1] * A.nt[2])
       coarsest_node<T, VIR>(A.qt, A.nt[0], A.nt[1], A.nt[2], A.tT, A.tV, A.et, A.wtop, mu);
@@ -371,7 +411,7 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
   Vec4<T>* wv = reinterpret_cast<Vec4<T>*>(smem_raw + align16(sizeof(T) * S * Sp));
   int4* rows = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(wv) +
                                        sizeof(Vec4<T>) * A.ntaps);
-  const long b = blockIdx.x;
+  const long b = bk.x;
   int k = 0;
   while (k + 1 < A.nlev && b >= A.lv[k + 1].tile_off) ++k;
   const T* __restrict__ q = A.lv[k].q;
@@ -465,6 +505,12 @@ __global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> 
       for (int c = 0; c < 6; ++c) wpart[6 * b + c] = hs * A.hc[c] * w6[c];
     }
   }
+}
+
+template <typename T, bool VIR, int G>
+__global__ void __launch_bounds__(kStencilThreads * G) k_stencil(StencilArgs<T> A,
+                                                                 double* __restrict__ wpart) {
+  k_stencil_body<T, VIR, G>(Blk::self(), A, wpart);
 }
 
 // Same evaluation without shared-memory staging, for stencils whose tile
@@ -571,7 +617,9 @@ template <typename T> static StencilArgs<T> stencil_args(Plan* p) {
 }
 
 // Whether the coarsest level rides on the stencil launch (extra blocks).
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 bool stencil_fuses_top(const Plan* p) { return p->levels >= 2 && !p->stencil_global && !p->prof; }
+#endif  // MLS6_DEVICE_ONLY
 
 template <typename T> int launch_stencil(Plan* p, bool vir, cudaStream_t st) {
   if (p->levels < 2) return 0;
@@ -634,19 +682,20 @@ template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
 // -------------------------------------------------------------- prolongation
 
 // e^{k,tot}_mu = e^k_mu + sum_nu prod_d Phi(mu_d/2 - nu_d) e^{k+1,tot}_nu.
-template <typename T>
-__global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
+template <typename T, int NP = 4>
+__device__ __forceinline__ void k_prolong_body(const Blk bk,const T* __restrict__ ef, int f0, int f1, int f2,
                           const T* __restrict__ etc_, int c0, int c1, int c2,
                           T* __restrict__ etf) {
   const long z = pdl_begin();
   ef += z; etc_ += z;
-  long mu = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long mu = (long)bk.x * blockDim.x + threadIdx.x;
   long np = (long)f0 * f1 * f2;
   if (mu >= np) return;
   int m[3] = {(int)(mu % f0), (int)((mu / f0) % f1), (int)(mu / ((long)f0 * f1))};
   int nc[3] = {c0, c1, c2};
-  int idx[3][4];
-  T wt[3][4];
+  constexpr int H = NP / 2;
+  int idx[3][NP];
+  T wt[3][NP];
   int cnt[3];
   for (int d = 0; d < 3; ++d) {
     if ((m[d] & 1) == 0) {
@@ -654,16 +703,13 @@ __global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
       idx[d][0] = wrapi(m[d] >> 1, nc[d]);
       wt[d][0] = T(1);
     } else {
-      cnt[d] = 4;
+      cnt[d] = NP;
       int h = (m[d] - 1) >> 1;  // coarse node left of mu
-      idx[d][0] = wrapi(h - 1, nc[d]);
-      idx[d][1] = wrapi(h, nc[d]);
-      idx[d][2] = wrapi(h + 1, nc[d]);
-      idx[d][3] = wrapi(h + 2, nc[d]);
-      wt[d][0] = T(-0.0625);
-      wt[d][1] = T(0.5625);
-      wt[d][2] = T(0.5625);
-      wt[d][3] = T(-0.0625);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {  // coarse nodes h - (H-1) .. h + H
+        idx[d][k] = wrapi(h - (H - 1) + k, nc[d]);
+        wt[d][k] = half_weight<NP, T>(k < H ? H - 1 - k : k - H);
+      }
     }
   }
   T acc = 0;
@@ -677,9 +723,16 @@ __global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
   etf[mu] = ef[mu] + acc;
 }
 
+template <typename T, int NP>
+__global__ void k_prolong(const T* __restrict__ ef, int f0, int f1, int f2,
+                          const T* __restrict__ etc_, int c0, int c1, int c2,
+                          T* __restrict__ etf) {
+  k_prolong_body<T, NP>(Blk::self(), ef, f0, f1, f2, etc_, c0, c1, c2, etf);
+}
+
 template <typename T> int launch_prolong(Plan* p, int k, cudaStream_t st) {
   const Level &F = p->lv[k], &C = p->lv[k + 1];
-  launch_pdl(k_prolong<T>, cdiv(F.np, kBlock), kBlock, 0, st, (const T*)p->d_e[k], F.n[0], F.n[1],
+  launch_pdl(p->order == 5 ? k_prolong<T, 6> : k_prolong<T, 4>, cdiv(F.np, kBlock), kBlock, 0, st, (const T*)p->d_e[k], F.n[0], F.n[1],
                                                      F.n[2], (const T*)p->d_et[k + 1], C.n[0],
                                                      C.n[1], C.n[2], (T*)p->d_et[k]);
   return 1;
@@ -702,8 +755,8 @@ struct ReduceArgs {
   int ng;
 };
 
-template <typename T, bool SLICES>
-__global__ void __launch_bounds__(kBlock) k_interp(
+template <typename T, bool SLICES, int NP = 4>
+__device__ __forceinline__ void k_interp_body(const Blk bk,
     const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ et,
     int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
     const T* __restrict__ floc, double cself, T* __restrict__ forces,
@@ -712,31 +765,32 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   sp += z; sidx += z; et += z; e0 += z; floc += z;
   __shared__ double sh[32 * 7];
   __shared__ bool last;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = bk.x * blockDim.x + threadIdx.x;
   T ea = T(0);
   if (i < N) {
     Vec4<T> p = sp[i];
     T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
     T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
     int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
-    T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
-    phi4(u0 - f0, wx, dx);
-    phi4(u1 - f1, wy, dy);
-    phi4(u2 - f2, wz, dz);
-    int ix[4];
+    constexpr int B0 = NP / 2 - 1;
+    T wx[NP], wy[NP], wz[NP], dx[NP], dy[NP], dz[NP];
+    phid<NP>(u0 - f0, wx, dx);
+    phid<NP>(u1 - f1, wy, dy);
+    phid<NP>(u2 - f2, wz, dz);
+    int ix[NP];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ix[k] = wrapi(b0 - 1 + k, n0);
+    for (int k = 0; k < NP; ++k) ix[k] = wrapi(b0 - B0 + k, n0);
     T acc = 0, g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int z = wrapi(b2 - 1 + c, n2);
+    for (int c = 0; c < NP; ++c) {
+      int z = wrapi(b2 - B0 + c, n2);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        int y = wrapi(b1 - 1 + b, n1);
+      for (int b = 0; b < NP; ++b) {
+        int y = wrapi(b1 - B0 + b, n1);
         const T* row = et + (long)n0 * (y + (long)n1 * z);
         T sx = 0, sdx = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < NP; ++a) {
           T v = row[ix[a]];
           sx += wx[a] * v;
           sdx += dx[a] * v;
@@ -764,8 +818,8 @@ __global__ void __launch_bounds__(kBlock) k_interp(
   // block adds the ng slice sums instead of every record (one block summing
   // ~7,600 records in FP64 took 22 us on a 1M-atom cube).  In a single wave
   // the slices would lengthen the kernel instead, and ng is 0.
-  if (SLICES && R.vir && (int)blockIdx.x < R.ng && threadIdx.x < 32) {
-    const long per = (R.nw + R.ng - 1) / R.ng, k0 = (long)blockIdx.x * per;
+  if (SLICES && R.vir && (int)bk.x < R.ng && threadIdx.x < 32) {
+    const long per = (R.nw + R.ng - 1) / R.ng, k0 = (long)bk.x * per;
     const long k1 = min(R.nw, k0 + per);
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (long k = k0 + threadIdx.x; k < k1; k += 32)
@@ -774,22 +828,31 @@ __global__ void __launch_bounds__(kBlock) k_interp(
 #pragma unroll
     for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
     if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) R.gsum[6 * blockIdx.x + c] = v[c];
+      for (int c = 0; c < 6; ++c) R.gsum[6 * bk.x + c] = v[c];
   }
   if (threadIdx.x == 0) {
-    epart[blockIdx.x] = s[0];
+    epart[bk.x] = s[0];
     __threadfence();
-    last = atomicAdd(R.ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(R.ticket, 1u) == bk.n - 1;
   }
   __syncthreads();
   if (last) {
     __threadfence();
     if (SLICES)
-      final_reduce(epart, gridDim.x, R.gsum, R.ng, R.vir, R.out, sh);
+      final_reduce(epart, bk.n, R.gsum, R.ng, R.vir, R.out, sh);
     else
-      final_reduce(epart, gridDim.x, R.wpart, R.nw, R.vir, R.out, sh);
+      final_reduce(epart, bk.n, R.wpart, R.nw, R.vir, R.out, sh);
     if (threadIdx.x == 0) *R.ticket = 0u;
   }
+}
+
+template <typename T, bool SLICES, int NP>
+__global__ void __launch_bounds__(kBlock) k_interp(
+    const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ et,
+    int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
+    const T* __restrict__ floc, double cself, T* __restrict__ forces,
+    double* __restrict__ atom_energy, double* __restrict__ epart, ReduceArgs R) {
+  k_interp_body<T, SLICES, NP>(Blk::self(), sp, sidx, N, et, n0, n1, n2, ih0, ih1, ih2, e0, floc, cself, forces, atom_energy, epart, R);
 }
 
 // Lorentz-Berthelot interpolation: the seven channel potentials e^{(m),tot}
@@ -797,7 +860,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
 // basis sum (both linear): e_i = sum_m xi_{i,6-m} e^{(m)}(x_i) and
 // F_i = F_i^loc + sum_m xi_{i,6-m} grad e^{(m)}(x_i); per-atom energy
 // -1/2 (e0_i + e_i) + 1/2 c_self C_ii with C_ii = 2 eps_i sigma_i^6.
-template <typename T>
+template <typename T, int NP>
 __global__ void __launch_bounds__(kBlock) k_interp_lb(
     const Vec4<T>* __restrict__ sp, const int* __restrict__ sidx, int N, const T* __restrict__ pot,
     long np, int n0, int n1, int n2, T ih0, T ih1, T ih2, const T* __restrict__ e0,
@@ -822,22 +885,23 @@ __global__ void __launch_bounds__(kBlock) k_interp_lb(
     T u0 = p.x * ih0, u1 = p.y * ih1, u2 = p.z * ih2;
     T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
     int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
-    T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
-    phi4(u0 - f0, wx, dx);
-    phi4(u1 - f1, wy, dy);
-    phi4(u2 - f2, wz, dz);
-    int ix[4];
+    constexpr int B0 = NP / 2 - 1;
+    T wx[NP], wy[NP], wz[NP], dx[NP], dy[NP], dz[NP];
+    phid<NP>(u0 - f0, wx, dx);
+    phid<NP>(u1 - f1, wy, dy);
+    phid<NP>(u2 - f2, wz, dz);
+    int ix[NP];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ix[k] = wrapi(b0 - 1 + k, n0);
+    for (int k = 0; k < NP; ++k) ix[k] = wrapi(b0 - B0 + k, n0);
     T acc = 0, g0 = 0, g1 = 0, g2 = 0;
-    for (int c = 0; c < 4; ++c) {
-      int z = wrapi(b2 - 1 + c, n2);
-      for (int b = 0; b < 4; ++b) {
-        int y = wrapi(b1 - 1 + b, n1);
+    for (int c = 0; c < NP; ++c) {
+      int z = wrapi(b2 - B0 + c, n2);
+      for (int b = 0; b < NP; ++b) {
+        int y = wrapi(b1 - B0 + b, n1);
         const long row = (long)n0 * (y + (long)n1 * z);
         T sx = 0, sdx = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < NP; ++a) {
           T v = 0;
 #pragma unroll
           for (int m = 0; m < 7; ++m) v += xi[6 - m] * pot[m * np + row + ix[a]];
@@ -878,7 +942,7 @@ template <typename T> int launch_interp_lb(Plan* p, T* forces, cudaStream_t st) 
   const int N = (int)p->N;
   ReduceArgs R = {p->d_wpart, wpart_used(p), 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1)};
-  launch_pdl(k_interp_lb<T>, cdiv(N, kBlock), kBlock, 0, st, 
+  launch_pdl(p->order == 5 ? k_interp_lb<T, 6> : k_interp_lb<T, 4>, cdiv(N, kBlock), kBlock, 0, st, 
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_lbpot, L1.np, L1.n[0],
       L1.n[1], L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]),
       (const T*)p->d_e0, (const T*)p->d_floc, (const T*)p->d_lbw, p->c_self, forces, p->d_epart,
@@ -896,7 +960,8 @@ int launch_interp(Plan* p, T* forces, double* atom_energy, bool vir, cudaStream_
   ReduceArgs R = {p->d_wpart, wpart_used(p), vir ? 1 : 0, p->d_out,
                   reinterpret_cast<unsigned*>(p->d_flag + 1), p->d_out + 8,
                   slices ? kReduceGroups : 0};
-  auto kern = slices ? k_interp<T, true> : k_interp<T, false>;
+  auto kern = p->order == 5 ? (slices ? k_interp<T, true, 6> : k_interp<T, false, 6>)
+                            : (slices ? k_interp<T, true, 4> : k_interp<T, false, 4>);
   launch_pdl(kern, cdiv(N, kBlock), kBlock, 0, st,
       (const Vec4<T>*)p->d_sorted, p->d_sorted_idx, N, (const T*)p->d_et[1], L1.n[0], L1.n[1],
       L1.n[2], (T)(1.0 / L1.h[0]), (T)(1.0 / L1.h[1]), (T)(1.0 / L1.h[2]), (const T*)p->d_e0,
@@ -946,6 +1011,7 @@ template <typename T> int prepare_grid_kernels(Plan* p) {
   return MLS6_OK;
 }
 
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 #define MLS6_INSTANTIATE(T)                                               \
   template int launch_anterp<T>(Plan*, cudaStream_t, int);                \
   template int launch_lb_weights<T>(Plan*, const T*, cudaStream_t);       \
@@ -960,4 +1026,5 @@ MLS6_INSTANTIATE(float)
 MLS6_INSTANTIATE(double)
 #undef MLS6_INSTANTIATE
 
+#endif  // MLS6_DEVICE_ONLY
 }  // namespace mls6

@@ -27,7 +27,10 @@ constexpr int kStencilThreads = 128;
 constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
 constexpr size_t kStencilSmemMax = 200 * 1024;  // dynamic shared memory of a stencil tile
 constexpr double kCellDiv = 2.0;  // cell width >= a / kCellDiv
+constexpr int kPairCluster = 1024;  // pair_split code of the cluster form
 constexpr int kPairSplitMax = 32;  // pair-kernel blocks are at most N * kPairSplitMax / kBlock
+
+__host__ __device__ inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
@@ -72,6 +75,7 @@ struct Plan {
   Level lv[kMaxLevels + 1];  // 1-based
   Smooth sm;                 // smoothing function
   double c_self;             // gamma(0)/a^6
+  int order = 3;             // interpolation order p: 3 (cubic) or 5 (quintic)
 
   // Level-1 stencil: taps m with |m h_1| < 2a, shared by all levels k < l
   // through the scale 2^(-6(k-1)) (Sec. II.A.4).  Taps are grouped in rows
@@ -194,7 +198,10 @@ template <typename T> int prepare_grid_kernels(Plan* p);
 template <typename T> int prepare_pair_kernels(Plan* p);
 int launch_reduce(Plan* p, bool vir, cudaStream_t st);
 int flag_status(int flag_word);  // mls6_eval.cu
+double lb_coef(int m);           // Lorentz-Berthelot channel coefficient (mls6_grid.cu)
 int pair_split(const Plan* p);  // default lanes per atom of the pair kernel (mls6_pair.cu)
+int pair_split_atom(const Plan* p);  // the default among the per-atom, warp and queue forms
+bool pair_cl_ok(const Plan* p);      // the cluster form (kPairCluster) applies
 bool pair_cluster_ok(const Plan* p);  // warp form usable (mls6_pair.cu)
 // virial partial records summed by the final reduction
 long pair_blocks(const Plan* p, int split);  // blocks of the pair kernel (mls6_pair.cu)
@@ -207,6 +214,18 @@ void tc_geometry(Plan* p);
 std::vector<uint32_t> tc_weight_table(const Plan* p);
 int prepare_stencil_tc(Plan* p);
 int launch_stencil_tc(Plan* p, bool vir, bool fuse_top, cudaStream_t st);
+// persistent batch execution (mls6_persist.cu)
+struct PersistExec;
+bool persist_eligible(const Plan* p);
+int persist_build(PersistExec** out, Plan* const* plans, int B, const int64_t* off,
+                  const double* cost, const void* pos, const void* c, void* forces, double* ew,
+                  int* flags, bool vir);
+int persist_set_wait(PersistExec* x, long long limit, long long withhold);
+int persist_launch(PersistExec* x, cudaStream_t st);
+void persist_free(PersistExec* x);
+const int* persist_error_word(const PersistExec* x);
+long long persist_items(const PersistExec* x);
+int persist_grid(const PersistExec* x);
 // tcgen05 stencil (mls6_stencil_mma.cu)
 bool stencil_mma_eligible(const Plan* p);
 long stencil_mma_tiles(const Plan* p);

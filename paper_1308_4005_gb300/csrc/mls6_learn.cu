@@ -13,10 +13,15 @@
 //              (mma.m16n8k16, FP32 accumulation); one warp per 16 atoms, the
 //              accumulator tiles of a layer are repacked in registers as the
 //              A operand of the next
-//   training   FP32 backward pass (per-atom activation gradients, per-chunk
-//              weight-gradient partials summed in a fixed order, so results
-//              are reproducible), Adam update of FP32 master weights, BF16
-//              fragments repacked after every step
+//   training   BF16 tensor-core backward pass: activation gradients
+//              dZ = (dZ_next W^T) (1 - h^2) per 16-atom warp tile with the
+//              transposed weights as B fragments (mma.m16n8k16, FP32
+//              accumulation, dZ kept as BF16); weight gradients X^T dZ1,
+//              H^T dZ per block of atoms from shared-memory tiles read as
+//              transposed fragments (ldmatrix .trans), bias gradients as
+//              products with a ones operand; per-block partials summed in a
+//              fixed order (results reproducible bit for bit); Adam update of
+//              FP32 master weights, BF16 fragments repacked after every step
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -35,7 +40,6 @@ namespace mls6 {
     if (e_ != cudaSuccess) return MLS6_ERR_CUDA; \
   } while (0)
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 constexpr int kNF = 128;                        // feature row (114 used)
 constexpr int kH = 64;                          // hidden width
@@ -48,7 +52,16 @@ constexpr int kNPar = kOffB4 + kNO;             // 17096
 // packed B fragments (uint2 per lane): layer 1 8x8 tiles, layers 2-3 4x8, layer 4 4x1
 constexpr int kPk1 = 0, kPk2 = kPk1 + 8 * 8 * 32, kPk3 = kPk2 + 4 * 8 * 32,
               kPk4 = kPk3 + 4 * 8 * 32, kPkN = kPk4 + 4 * 1 * 32;
-constexpr int kChunk = 512;                     // atoms per weight-gradient partial
+// transposed weights for the backward pass (B[k][n] = W[n][k]): W4^T one
+// k-step (K = 8 padded to 16) x 8 tiles, W3^T and W2^T 4 x 8
+constexpr int kPkT4 = kPkN, kPkT3 = kPkT4 + 1 * 8 * 32, kPkT2 = kPkT3 + 4 * 8 * 32,
+              kPkAll = kPkT2 + 4 * 8 * 32;
+// weight gradients: blocks of kWB atoms staged in shared memory, at most
+// kWGrid thread blocks (partials), rows padded by 8 BF16 (16 bytes) so the
+// eight rows an ldmatrix reads fall in distinct banks
+constexpr int kWB = 64, kWGrid = 152;
+constexpr int kXS = kNF + 8, kHS = kH + 8;
+constexpr int kWStage = kWB * (kXS + 6 * kHS + kNO);  // BF16 elements per stage
 
 struct Mlp {
   float* d_par = nullptr;   // FP32 master weights
@@ -64,10 +77,10 @@ struct Mlp {
   __nv_bfloat16* d_X = nullptr;   // features for mls6_mlp_apply
   float* d_Y = nullptr;           // outputs
   __nv_bfloat16* d_H = nullptr;   // 3 x N x 64 activations (training)
-  float* d_D = nullptr;           // 3 x N x 64 activation gradients
-  float* d_dY = nullptr;          // N x 8
-  float* d_part = nullptr;        // chunks x kNPar partial gradients
-  double* d_lpart = nullptr;      // chunks loss partials
+  __nv_bfloat16* d_D = nullptr;   // 3 x N x 64 activation gradients dZ1..dZ3
+  __nv_bfloat16* d_dY = nullptr;  // N x 8 output gradients
+  float* d_part = nullptr;        // blocks x kNPar partial gradients
+  double* d_lpart = nullptr;      // loss partials, one per backward block
   float* d_grad = nullptr;        // kNPar
   double* d_loss = nullptr;
 };
@@ -210,9 +223,35 @@ __global__ void __launch_bounds__(3 * kFA) k_features(
 // B fragment of mma.m16n8k16 for weights W (K x N row-major, row = input):
 // lane (g = lane/4, c2 = 2*(lane%4)) holds W[16ks+c2..+1][8nt+g] and
 // W[16ks+c2+8..+9][8nt+g].
+// Transposed (backward) fragments: B[k][n] = W[n][k] for W = W4, W3, W2
+// (row = input n, column = output k); k >= the layer's outputs is zero.
+__device__ __forceinline__ float wt_at(const float* W, int NO, int k, int n) {
+  return k < NO ? W[n * NO + k] : 0.f;
+}
+
 __global__ void k_mlp_pack(const float* __restrict__ par, uint2* __restrict__ pk) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= kPkN) return;
+  if (t >= kPkAll) return;
+  if (t >= kPkN) {
+    int off, NO, base;
+    if (t < kPkT3) {
+      off = kOffW4; NO = kNO; base = kPkT4;
+    } else if (t < kPkT2) {
+      off = kOffW3; NO = kH; base = kPkT3;
+    } else {
+      off = kOffW2; NO = kH; base = kPkT2;
+    }
+    const int r = t - base, lane = r & 31, tile = r >> 5;
+    const int ks = tile / 8, nt = tile % 8;
+    const int g = lane >> 2, c2 = (lane & 3) * 2;
+    const int n = 8 * nt + g, k = 16 * ks + c2;
+    const float* W = par + off;
+    uint2 v;
+    v.x = pack_bf16(wt_at(W, NO, k, n), wt_at(W, NO, k + 1, n));
+    v.y = pack_bf16(wt_at(W, NO, k + 8, n), wt_at(W, NO, k + 9, n));
+    pk[t] = v;
+    return;
+  }
   int off, NT, NO, base;
   if (t < kPk2) {
     off = kOffW1; NT = 8; NO = kH; base = kPk1;
@@ -359,149 +398,303 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(const __nv_bfloat16* __restrict
   }
 }
 
-// Backward through the activations (FP32, one thread per atom):
-// dY = 2 (y - t) / N on outputs 0..2; dZ3 = (dY W4^T) (1 - h3^2);
-// dZ2 = (dZ3 W3^T) (1 - h2^2); dZ1 = (dZ2 W2^T) (1 - h1^2).
+// Backward through the activations on the tensor cores, one warp per
+// 16-atom tile (the forward pass's tiling): dY = 2 (y - t) / N on outputs
+// 0..2 (BF16, stored for the weight gradients), then per layer
+//   dZ3 = (dY W4^T) (1 - h3^2),  dZ2 = (dZ3 W3^T) (1 - h2^2),
+//   dZ1 = (dZ2 W2^T) (1 - h1^2),
+// each product an mma over the transposed-weight fragments with FP32
+// accumulators; the factor (1 - h^2) uses the stored BF16 activations at
+// the accumulator positions, and the result is packed (BF16) both as the
+// next layer's A fragments and into D for the weight gradients.  Loss
+// partials: one per block, summed in a fixed order by k_mlp_reduce.
+__device__ __forceinline__ void act_grad(const float (&acc)[8][4], const uint32_t* __restrict__ Hl,
+                                         long ra, long rb, bool va, bool vb, int c2,
+                                         uint32_t* __restrict__ Dl, uint32_t (&A)[4][4]) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int w = (8 * nt + c2) >> 1;
+    float ha0 = 0.f, ha1 = 0.f, hb0 = 0.f, hb1 = 0.f;
+    if (va) {
+      const uint32_t u = Hl[ra * (kH / 2) + w];
+      const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&u);
+      ha0 = __low2float(h);
+      ha1 = __high2float(h);
+    }
+    if (vb) {
+      const uint32_t u = Hl[rb * (kH / 2) + w];
+      const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&u);
+      hb0 = __low2float(h);
+      hb1 = __high2float(h);
+    }
+    const uint32_t pa = pack_bf16(acc[nt][0] * (1.f - ha0 * ha0), acc[nt][1] * (1.f - ha1 * ha1));
+    const uint32_t pb = pack_bf16(acc[nt][2] * (1.f - hb0 * hb0), acc[nt][3] * (1.f - hb1 * hb1));
+    // tile nt is half (nt & 1) of k-step nt / 2 of the next product
+    A[nt >> 1][(nt & 1) * 2 + 0] = pa;
+    A[nt >> 1][(nt & 1) * 2 + 1] = pb;
+    if (va) Dl[ra * (kH / 2) + w] = pa;
+    if (vb) Dl[rb * (kH / 2) + w] = pb;
+  }
+}
+
+__device__ __forceinline__ void back_product(const uint32_t (&A)[4][4],
+                                             const uint2* __restrict__ sw, int lane,
+                                             float (&acc)[8][4]) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const uint2 b = sw[(ks * 8 + nt) * 32 + lane];
+      mma16816(acc[nt], A[ks][0], A[ks][1], A[ks][2], A[ks][3], b.x, b.y);
+    }
+}
+
 __global__ void __launch_bounds__(128) k_mlp_bwd(const float* __restrict__ Y,
                                                  const float* __restrict__ T, long N,
                                                  float inv_n, const __nv_bfloat16* __restrict__ H,
-                                                 const float* __restrict__ par,
-                                                 float* __restrict__ D, float* __restrict__ dY,
+                                                 const uint2* __restrict__ pk,
+                                                 __nv_bfloat16* __restrict__ D,
+                                                 __nv_bfloat16* __restrict__ dYb,
                                                  double* __restrict__ lpart) {
-  __shared__ float w2[kH * kH], w3[kH * kH], w4[kH * kNO];
+  constexpr int kT = kPkAll - kPkN;
+  __shared__ uint2 sw[kT];
   __shared__ double sh[32];
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    w2[i] = par[kOffW2 + i];
-    w3[i] = par[kOffW3 + i];
-  }
-  for (int i = threadIdx.x; i < kH * kNO; i += blockDim.x) w4[i] = par[kOffW4 + i];
+  for (int i = threadIdx.x; i < kT; i += blockDim.x) sw[i] = pk[kPkN + i];
   __syncthreads();
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, c2 = (lane & 3) * 2;
+  const uint32_t* Hw = reinterpret_cast<const uint32_t*>(H);
+  uint32_t* Dw = reinterpret_cast<uint32_t*>(D);
+  uint32_t* dYw = reinterpret_cast<uint32_t*>(dYb);
   double l = 0.0;
-  if (i < N) {
-    float dy[3];
-    for (int c = 0; c < 3; ++c) {
-      const float r = Y[i * kNO + c] - T[i * 3 + c];
-      l += (double)r * r;
-      dy[c] = 2.f * r * inv_n;
-    }
-    for (int c = 0; c < kNO; ++c) dY[i * kNO + c] = c < 3 ? dy[c] : 0.f;
-    const __nv_bfloat16* h1 = H + i * kH;
-    const __nv_bfloat16* h2 = H + (N + i) * kH;
-    const __nv_bfloat16* h3 = H + (2 * N + i) * kH;
-    float d3[kH], d2[kH];
+  for (long tile = (long)blockIdx.x * 4 + warp; tile * 16 < N; tile += (long)gridDim.x * 4) {
+    const long ra = tile * 16 + g, rb = ra + 8;
+    const bool va = ra < N, vb = rb < N;
+    float dy[4] = {0.f, 0.f, 0.f, 0.f};  // (ra, c2), (ra, c2+1), (rb, c2), (rb, c2+1)
 #pragma unroll
-    for (int j = 0; j < kH; ++j) {
-      const float h = __bfloat162float(h3[j]);
-      d3[j] = (dy[0] * w4[j * kNO] + dy[1] * w4[j * kNO + 1] + dy[2] * w4[j * kNO + 2]) *
-              (1.f - h * h);
+    for (int q = 0; q < 4; ++q) {
+      const long r = q < 2 ? ra : rb;
+      const int c = c2 + (q & 1);
+      if ((q < 2 ? va : vb) && c < 3) {
+        const float e = Y[r * kNO + c] - T[r * 3 + c];
+        l += (double)e * e;
+        dy[q] = 2.f * e * inv_n;
+      }
     }
-    for (int j = 0; j < kH; ++j) {
-      float s = 0.f;
+    const uint32_t da = pack_bf16(dy[0], dy[1]), db = pack_bf16(dy[2], dy[3]);
+    if (va) dYw[ra * (kNO / 2) + (c2 >> 1)] = da;
+    if (vb) dYw[rb * (kNO / 2) + (c2 >> 1)] = db;
+    // dY W4^T: one k-step, columns 8..15 of A are zero
+    float acc[8][4];
 #pragma unroll
-      for (int k = 0; k < kH; ++k) s += d3[k] * w3[j * kH + k];
-      const float h = __bfloat162float(h2[j]);
-      d2[j] = s * (1.f - h * h);
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+      const uint2 b = sw[(kPkT4 - kPkN) + nt * 32 + lane];
+      mma16816(acc[nt], da, db, 0u, 0u, b.x, b.y);
     }
-    float* D1 = D + i * kH;
-    float* D2 = D + (N + i) * kH;
-    float* D3 = D + (2 * N + i) * kH;
-    for (int j = 0; j < kH; ++j) {
-      float s = 0.f;
-#pragma unroll
-      for (int k = 0; k < kH; ++k) s += d2[k] * w2[j * kH + k];
-      const float h = __bfloat162float(h1[j]);
-      D1[j] = s * (1.f - h * h);
-      D2[j] = d2[j];
-      D3[j] = d3[j];
-    }
+    uint32_t A[4][4];
+    act_grad(acc, Hw + 2 * N * (kH / 2), ra, rb, va, vb, c2, Dw + 2 * N * (kH / 2), A);
+    back_product(A, sw + (kPkT3 - kPkN), lane, acc);
+    act_grad(acc, Hw + N * (kH / 2), ra, rb, va, vb, c2, Dw + N * (kH / 2), A);
+    back_product(A, sw + (kPkT2 - kPkN), lane, acc);
+    act_grad(acc, Hw, ra, rb, va, vb, c2, Dw, A);
   }
   const double s = block_sum(l, sh);
   if (threadIdx.x == 0) lpart[blockIdx.x] = s;
 }
 
-// Weight gradients of one chunk of atoms: dW = sum_i a_i (x) d_i and
-// db = sum_i d_i for the four layers (a = X, h1, h2, h3; d = dZ1, dZ2, dZ3,
-// dY).  Each thread owns parameters p = tid, tid + blockDim, ...; the
-// chunk's rows are staged 16 atoms at a time.
+// Weight gradients on the tensor cores.  Thread block c sums the atoms of
+// blocks [c per, (c+1) per) of kWB atoms (per = ceil(blocks / kWGrid)):
+//   dW1 = X^T dZ1 (128 x 64), dW2 = H1^T dZ2, dW3 = H2^T dZ3 (64 x 64),
+//   dW4 = H3^T dY (64 x 8), db = column sums of dZ1, dZ2, dZ3, dY.
+// Each block of atoms is copied (cp.async, 16-byte pieces, rows past N
+// zero-filled) into one of two shared-memory stages while the other is
+// used.  Atoms are the K dimension: the A operand (activations transposed)
+// and the B operand (gradients) are both read from row-major [atom][column]
+// tiles with ldmatrix .trans.  Warp w owns rows 16w.. of dW1, rows 16w.. of
+// dW2 and dW4 (w < 4) or of dW3 (w >= 4); the bias sums are mma products
+// with an all-ones A (every row of the result is the column sum), taken by
+// warps 0 (b2), 1 (b4), 4 (b1), 5 (b3) from fragments they already hold.
+// The partial of block c is written to part[c][*]; k_mlp_reduce sums the
+// partials in block order, so the result is reproducible bit for bit.
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm2t(uint32_t (&r)[2], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+// A fragments of rows 16 m0.. (the activation columns) for k-step ks of a
+// stage tile [atom][column] with row stride S: matrices (atoms 0-7 / 8-15)
+// x (columns 0-7 / 8-15) in the order a0 a1 a2 a3 of the mma.
+template <int S>
+__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16* t, int ks, int m0,
+                                       int lane) {
+  const int j = lane >> 3, r = lane & 7;
+  ldsm4t(a, t + (16 * ks + r + 8 * (j >> 1)) * S + 16 * m0 + 8 * (j & 1));
+}
+
+// B fragments of column tiles nt0, nt0+1 for k-step ks: b[0..1] for nt0,
+// b[2..3] for nt0+1.
+template <int S>
+__device__ __forceinline__ void frag_b2(uint32_t (&b)[4], const __nv_bfloat16* t, int ks, int nt0,
+                                        int lane) {
+  const int j = lane >> 3, r = lane & 7;
+  ldsm4t(b, t + (16 * ks + r + 8 * (j & 1)) * S + 8 * (nt0 + (j >> 1)));
+}
+
 __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restrict__ X,
                                                    const __nv_bfloat16* __restrict__ H,
-                                                   const float* __restrict__ D,
-                                                   const float* __restrict__ dY, long N,
-                                                   float* __restrict__ part) {
-  constexpr int R = 16;
-  __shared__ float sa[R][kNF + 3 * kH];   // x, h1, h2, h3
-  __shared__ float sd[R][3 * kH + kNO];   // dz1, dz2, dz3, dy
-  constexpr int kPer = (kNPar + 255) / 256;
-  float acc[kPer];
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) acc[j] = 0.f;
-  const long i0 = (long)blockIdx.x * kChunk, i1 = min(N, i0 + kChunk);
-  for (long r0 = i0; r0 < i1; r0 += R) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < R * (kNF + 3 * kH); t += blockDim.x) {
-      const int r = t / (kNF + 3 * kH), c = t % (kNF + 3 * kH);
+                                                   const __nv_bfloat16* __restrict__ D,
+                                                   const __nv_bfloat16* __restrict__ dY, long N,
+                                                   long per, float* __restrict__ part) {
+  extern __shared__ __align__(16) __nv_bfloat16 stg[];  // two stages of kWStage
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, c2 = (lane & 3) * 2;
+  const long nblk = cdiv(N, (long)kWB);
+  const long b0 = (long)blockIdx.x * per, b1 = min(nblk, b0 + per);
+  // stage layout: X [kWB][kXS], H1..H3 [kWB][kHS], dZ1..dZ3 [kWB][kHS], dY [kWB][kNO]
+  auto sx = [&](int st) { return stg + (size_t)st * kWStage; };
+  auto sh = [&](int st, int l) { return sx(st) + kWB * kXS + l * kWB * kHS; };
+  auto sd = [&](int st, int l) { return sx(st) + kWB * kXS + (3 + l) * kWB * kHS; };
+  auto sy = [&](int st) { return sx(st) + kWB * kXS + 6 * kWB * kHS; };
+  auto stage = [&](int st, long blk) {
+    const long r0 = blk * kWB;
+    constexpr int kPieces = kNF / 8 + 6 * (kH / 8) + 1;  // 16-byte pieces per atom row
+    for (int t = threadIdx.x; t < kWB * kPieces; t += blockDim.x) {
+      const int r = t / kPieces, q = t % kPieces;
       const long i = r0 + r;
-      float v = 0.f;
-      if (i < i1) {
-        if (c < kNF)
-          v = __bfloat162float(X[i * kNF + c]);
-        else {
-          const int l = (c - kNF) / kH, j = (c - kNF) % kH;
-          v = __bfloat162float(H[((long)l * N + i) * kH + j]);
-        }
-      }
-      sa[r][c] = v;
-    }
-    for (int t = threadIdx.x; t < R * (3 * kH + kNO); t += blockDim.x) {
-      const int r = t / (3 * kH + kNO), c = t % (3 * kH + kNO);
-      const long i = r0 + r;
-      float v = 0.f;
-      if (i < i1) {
-        if (c < 3 * kH) {
-          const int l = c / kH, j = c % kH;
-          v = D[((long)l * N + i) * kH + j];
-        } else {
-          v = dY[i * kNO + (c - 3 * kH)];
-        }
-      }
-      sd[r][c] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int p = threadIdx.x + j * 256;
-      if (p >= kNPar) break;
-      int ac, dc;  // column of a (or -1 for a bias) and of d
-      if (p < kOffB1) {
-        ac = p / kH; dc = p % kH;
-      } else if (p < kOffW2) {
-        ac = -1; dc = p - kOffB1;
-      } else if (p < kOffB2) {
-        ac = kNF + (p - kOffW2) / kH; dc = kH + (p - kOffW2) % kH;
-      } else if (p < kOffW3) {
-        ac = -1; dc = kH + (p - kOffB2);
-      } else if (p < kOffB3) {
-        ac = kNF + kH + (p - kOffW3) / kH; dc = 2 * kH + (p - kOffW3) % kH;
-      } else if (p < kOffW4) {
-        ac = -1; dc = 2 * kH + (p - kOffB3);
-      } else if (p < kOffB4) {
-        ac = kNF + 2 * kH + (p - kOffW4) / kNO; dc = 3 * kH + (p - kOffW4) % kNO;
+      const bool ok = i < N;
+      const long ic = ok ? i : 0;
+      const __nv_bfloat16* src;
+      __nv_bfloat16* dst;
+      if (q < kNF / 8) {
+        src = X + ic * kNF + 8 * q;
+        dst = sx(st) + r * kXS + 8 * q;
+      } else if (q < kNF / 8 + 6 * (kH / 8)) {
+        const int u = q - kNF / 8, l = u / (kH / 8), c = u % (kH / 8);
+        src = (l < 3 ? H + ((long)l * N + ic) * kH : D + ((long)(l - 3) * N + ic) * kH) + 8 * c;
+        dst = (l < 3 ? sh(st, l) : sd(st, l - 3)) + r * kHS + 8 * c;
       } else {
-        ac = -1; dc = 3 * kH + (p - kOffB4);
+        src = dY + ic * kNO;
+        dst = sy(st) + r * kNO;
       }
-      float s = 0.f;
-      if (ac >= 0)
-        for (int r = 0; r < R; ++r) s += sa[r][ac] * sd[r][dc];
-      else
-        for (int r = 0; r < R; ++r) s += sd[r][dc];
-      acc[j] += s;
+      cp_async16(dst, src, ok ? 16 : 0);
     }
-  }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  float a1[8][4], a23[8][4], a4[4], ab[8][4];
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int p = threadIdx.x + j * 256;
-    if (p < kNPar) part[(long)blockIdx.x * kNPar + p] = acc[j];
+  for (int n = 0; n < 8; ++n)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a1[n][c] = a23[n][c] = ab[n][c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) a4[c] = 0.f;
+  const uint32_t one = 0x3F803F80u;  // two BF16 ones
+
+  if (b0 < b1) stage(0, b0);
+  for (long blk = b0; blk < b1; ++blk) {
+    const int st = (int)((blk - b0) & 1);
+    if (blk + 1 < b1) {
+      stage(st ^ 1, blk + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const int l23 = warp < 4 ? 0 : 1;           // dW2 (H1, dZ2) or dW3 (H2, dZ3)
+    const int m23 = warp & 3;
+#pragma unroll
+    for (int ks = 0; ks < kWB / 16; ++ks) {
+      uint32_t a[4], b[4][4];
+      // dW1 rows 16 warp..: X^T dZ1
+      frag_a<kXS>(a, sx(st), ks, warp, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) frag_b2<kHS>(b[q], sd(st, 0), ks, 2 * q, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        mma16816(a1[2 * q], a[0], a[1], a[2], a[3], b[q][0], b[q][1]);
+        mma16816(a1[2 * q + 1], a[0], a[1], a[2], a[3], b[q][2], b[q][3]);
+      }
+      if (warp == 4)  // b1: column sums of dZ1
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          mma16816(ab[2 * q], one, one, one, one, b[q][0], b[q][1]);
+          mma16816(ab[2 * q + 1], one, one, one, one, b[q][2], b[q][3]);
+        }
+      // dW2 (warps 0-3) / dW3 (warps 4-7)
+      frag_a<kHS>(a, sh(st, l23), ks, m23, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) frag_b2<kHS>(b[q], sd(st, 1 + l23), ks, 2 * q, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        mma16816(a23[2 * q], a[0], a[1], a[2], a[3], b[q][0], b[q][1]);
+        mma16816(a23[2 * q + 1], a[0], a[1], a[2], a[3], b[q][2], b[q][3]);
+      }
+      if (warp == 0 || warp == 5)  // b2 (dZ2) / b3 (dZ3)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          mma16816(ab[2 * q], one, one, one, one, b[q][0], b[q][1]);
+          mma16816(ab[2 * q + 1], one, one, one, one, b[q][2], b[q][3]);
+        }
+      if (warp < 4) {  // dW4 rows 16 warp..: H3^T dY (one column tile)
+        uint32_t by[2];
+        {
+          const int j = (lane >> 3) & 1, r = lane & 7;
+          ldsm2t(by, sy(st) + (16 * ks + r + 8 * j) * kNO);
+        }
+        frag_a<kHS>(a, sh(st, 2), ks, warp, lane);
+        mma16816(a4, a[0], a[1], a[2], a[3], by[0], by[1]);
+        if (warp == 1) mma16816(ab[0], one, one, one, one, by[0], by[1]);  // b4
+      }
+    }
+    __syncthreads();  // the stage is refilled two iterations later
+  }
+
+  // partial of this block, parameter order of the master weights
+  float* P = part + (long)blockIdx.x * kNPar;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int m = g + 8 * (c >> 1), n = 8 * nt + c2 + (c & 1);
+      P[kOffW1 + (16 * warp + m) * kH + n] = a1[nt][c];
+      P[(warp < 4 ? kOffW2 : kOffW3) + (16 * (warp & 3) + m) * kH + n] = a23[nt][c];
+    }
+  if (warp < 4)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      P[kOffW4 + (16 * warp + g + 8 * (c >> 1)) * kNO + c2 + (c & 1)] = a4[c];
+  if (g == 0) {  // row 0 of the ones products
+    if (warp == 4 || warp == 0 || warp == 5)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int off = warp == 4 ? kOffB1 : (warp == 0 ? kOffB2 : kOffB3);
+        P[off + 8 * nt + c2] = ab[nt][0];
+        P[off + 8 * nt + c2 + 1] = ab[nt][1];
+      }
+    if (warp == 1) {
+      P[kOffB4 + c2] = ab[0][0];
+      P[kOffB4 + c2 + 1] = ab[0][1];
+    }
   }
 }
 
@@ -566,6 +759,17 @@ static uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
+// Launch geometry of the training kernels (a function of N only, so the
+// partial sums and hence the results do not depend on the device).
+static long fwd_blocks(long N) { return std::min(cdiv(cdiv(N, 16L), 4L), 152L * 8); }
+static long bwd_blocks(long N) { return fwd_blocks(N); }
+static void wgrad_geometry(long N, long& grid, long& per) {
+  const long nblk = cdiv(N, (long)kWB);
+  per = cdiv(nblk, (long)kWGrid);
+  grid = per > 0 ? cdiv(nblk, per) : 0;
+}
+constexpr size_t kWSmem = 2 * (size_t)kWStage * sizeof(__nv_bfloat16);
+
 static int grow(Mlp* m, long N) {
   if (N <= m->cap) return MLS6_OK;
   void* bufs[] = {m->d_X, m->d_Y, m->d_H, m->d_D, m->d_dY, m->d_part, m->d_lpart};
@@ -579,13 +783,13 @@ static int grow(Mlp* m, long N) {
   m->d_part = nullptr;
   m->d_lpart = nullptr;
   m->cap = 0;
-  const long nch = cdiv(N, kChunk), nbl = cdiv(N, 128);
+  const long nbl = bwd_blocks(N);
   if (cudaMalloc((void**)&m->d_X, sizeof(__nv_bfloat16) * kNF * N) != cudaSuccess ||
       cudaMalloc((void**)&m->d_Y, sizeof(float) * kNO * N) != cudaSuccess ||
       cudaMalloc((void**)&m->d_H, sizeof(__nv_bfloat16) * 3 * kH * N) != cudaSuccess ||
-      cudaMalloc((void**)&m->d_D, sizeof(float) * 3 * kH * N) != cudaSuccess ||
-      cudaMalloc((void**)&m->d_dY, sizeof(float) * kNO * N) != cudaSuccess ||
-      cudaMalloc((void**)&m->d_part, sizeof(float) * kNPar * nch) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_D, sizeof(__nv_bfloat16) * 3 * kH * N) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_dY, sizeof(__nv_bfloat16) * kNO * N) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_part, sizeof(float) * kNPar * kWGrid) != cudaSuccess ||
       cudaMalloc((void**)&m->d_lpart, sizeof(double) * nbl) != cudaSuccess)
     return MLS6_ERR_NOMEM;
   m->cap = N;
@@ -593,15 +797,14 @@ static int grow(Mlp* m, long N) {
 }
 
 static int repack(Mlp* m) {
-  k_mlp_pack<<<cdiv(kPkN, 256), 256, 0, m->stream>>>(m->d_par, m->d_pack);
+  k_mlp_pack<<<cdiv(kPkAll, 256), 256, 0, m->stream>>>(m->d_par, m->d_pack);
   CK(cudaGetLastError());
   return MLS6_OK;
 }
 
 static int forward(Mlp* m, const void* X, long N, float* Y, bool store) {
   if (N <= 0) return MLS6_OK;
-  const long tiles = cdiv(N, 16);
-  const long nb = std::min(cdiv(tiles, 4), 152L * 8);
+  const long nb = fwd_blocks(N);
   if (store)
     k_mlp_fwd<true><<<nb, 128, 0, m->stream>>>((const __nv_bfloat16*)X, N, m->d_pack, m->d_par,
                                                Y, m->d_H);
@@ -617,11 +820,13 @@ static int gradient(Mlp* m, const void* X, const float* T, long N) {
   if (rc) return rc;
   rc = forward(m, X, N, m->d_Y, true);
   if (rc) return rc;
-  const long nbl = cdiv(N, 128), nch = cdiv(N, kChunk);
-  k_mlp_bwd<<<nbl, 128, 0, m->stream>>>(m->d_Y, T, N, 1.0f / (float)N, m->d_H, m->d_par, m->d_D,
-                                        m->d_dY, m->d_lpart);
-  k_mlp_wgrad<<<nch, 256, 0, m->stream>>>((const __nv_bfloat16*)X, m->d_H, m->d_D, m->d_dY, N,
-                                          m->d_part);
+  const long nbl = bwd_blocks(N);
+  long nch, per;
+  wgrad_geometry(N, nch, per);
+  k_mlp_bwd<<<nbl, 128, 0, m->stream>>>(m->d_Y, T, N, 1.0f / (float)N, m->d_H, m->d_pack,
+                                        m->d_D, m->d_dY, m->d_lpart);
+  k_mlp_wgrad<<<nch, 256, kWSmem, m->stream>>>((const __nv_bfloat16*)X, m->d_H, m->d_D, m->d_dY,
+                                               N, per, m->d_part);
   k_mlp_reduce<<<cdiv(kNPar, 256), 256, 0, m->stream>>>(m->d_part, (int)nch, m->d_lpart,
                                                        (int)nbl, 1.0 / (double)N, m->d_grad,
                                                        m->d_loss);
@@ -675,11 +880,17 @@ int mls6_mlp_create(mls6_mlp_t** out, uint64_t seed) {
       cudaMalloc((void**)&m->d_m, sizeof(float) * kNPar) != cudaSuccess ||
       cudaMalloc((void**)&m->d_v, sizeof(float) * kNPar) != cudaSuccess ||
       cudaMalloc((void**)&m->d_grad, sizeof(float) * kNPar) != cudaSuccess ||
-      cudaMalloc((void**)&m->d_pack, sizeof(uint2) * kPkN) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_pack, sizeof(uint2) * kPkAll) != cudaSuccess ||
       cudaMalloc((void**)&m->d_norm, sizeof(float) * 2 * kNF) != cudaSuccess ||
       cudaMalloc((void**)&m->d_loss, sizeof(double)) != cudaSuccess) {
     free_mlp(m);
     return MLS6_ERR_NOMEM;
+  }
+  // two shared-memory stages of the weight-gradient kernel (above 48 KB)
+  if (cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kWSmem) != cudaSuccess) {
+    free_mlp(m);
+    return MLS6_ERR_CUDA;
   }
   // Glorot-uniform weights from SplitMix64, zero biases, outputs 3..7 zero
   std::vector<float> p(kNPar, 0.f);
@@ -754,6 +965,7 @@ int mls6_mlp_set_norm(mls6_mlp_t* mm, const float* shift, const float* scale, fl
 int mls6_mlp_features(mls6_plan_t* plan, const mls6_mlp_t* mm, void* out, int fmt) {
   if (!plan || !mm || (fmt != 0 && fmt != 1)) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
+  if (p->order != 3) return MLS6_ERR_ORDER;  // features are defined on the cubic basis
   if (p->N > 0 && !out) return MLS6_ERR_ARG;
   Mlp* m = const_cast<Mlp*>(reinterpret_cast<const Mlp*>(mm));
   return p->prec == MLS6_FP64 ? features_t<double>(p, m, out, fmt, false, p->stream)
@@ -767,7 +979,7 @@ int mls6_mlp_forward(mls6_mlp_t* mm, const void* X, int64_t N, float* Y) {
 
 int mls6_mlp_grad(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, float* grad,
                   double* loss) {
-  if (!mm || N < 1 || !X || !T) return MLS6_ERR_ARG;
+  if (!mm || N < 1 || !X || !T || (reinterpret_cast<uintptr_t>(X) & 15)) return MLS6_ERR_ARG;
   Mlp* m = reinterpret_cast<Mlp*>(mm);
   int rc = gradient(m, X, T, N);
   if (rc) return rc;
@@ -779,7 +991,8 @@ int mls6_mlp_grad(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, floa
 
 int mls6_mlp_train_step(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, float lr,
                         double* loss) {
-  if (!mm || N < 1 || !X || !T || !(lr > 0.f)) return MLS6_ERR_ARG;
+  if (!mm || N < 1 || !X || !T || !(lr > 0.f) || (reinterpret_cast<uintptr_t>(X) & 15))
+    return MLS6_ERR_ARG;
   Mlp* m = reinterpret_cast<Mlp*>(mm);
   int rc = gradient(m, X, T, N);
   if (rc) return rc;
@@ -798,6 +1011,7 @@ int mls6_mlp_apply(mls6_plan_t* plan, mls6_mlp_t* mm, void* forces) {
   if (!plan || !mm) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   Mlp* m = reinterpret_cast<Mlp*>(mm);
+  if (p->order != 3) return MLS6_ERR_ORDER;
   const long N = p->N;
   if (N == 0) return MLS6_OK;
   if (!forces) return MLS6_ERR_ARG;

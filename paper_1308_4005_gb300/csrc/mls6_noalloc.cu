@@ -10,8 +10,6 @@
 // whose allocator must not be bypassed.  The per-node virial partials it
 // needs live in one file-scope device array of fixed size instead of
 // plan-owned workspace.
-#include <mutex>
-
 #include "mls6_device.cuh"
 
 namespace mls6 {
@@ -21,29 +19,17 @@ namespace mls6 {
 constexpr int kNoAllocMaxNodes = 4096;
 static __device__ __align__(256) double g_coarse_scratch[6 * kNoAllocMaxNodes];
 
-// Host-side address of g_coarse_scratch on each device, looked up once per
-// device (the symbol's host name is not a device address).
-constexpr int kNoAllocMaxDevices = 64;
-static double* g_scratch_ptr[kNoAllocMaxDevices] = {};
-static std::mutex g_scratch_mu;
-
+// Device address of g_coarse_scratch in the current context (the symbol's
+// host name is not a device address).  Looked up on every call rather than
+// cached: after a device reset or a re-created primary context a cached
+// address would point into a dead context.
 static int scratch_for_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_coarse_scratch) != cudaSuccess || !ptr) {
     cudaGetLastError();
     return MLS6_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return MLS6_ERR_SIZE;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_coarse_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return MLS6_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<double*>(ptr);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(ptr);
   return MLS6_OK;
 }
 

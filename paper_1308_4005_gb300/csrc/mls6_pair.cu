@@ -11,7 +11,6 @@
 
 namespace mls6 {
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 template <typename T> struct PairArgs {
   Box3<T> box;
@@ -80,14 +79,14 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdiv
 // pair coefficient is C_ij = lbw_i lbw_j ((sigma_i + sigma_j)/2)^6, and the
 // outputs are e0_i = sum_j C_ij g_0 and F_i = -sum_j C_ij g_0'/r d.
 template <typename T, bool VIR, int S, bool LB = false, bool GEN = false>
-__global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
+__device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
                                                   PairArgs<T> g, T* __restrict__ e0,
                                                   T* __restrict__ floc,
                                                   double* __restrict__ wpart,
-                                                  const T* __restrict__ lbw = nullptr) {
+                                                  const T* __restrict__ lbw) {
   __shared__ double sh[32 * 6];
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gid = bk.x * blockDim.x + threadIdx.x;
   const int i = gid / S, sub = gid % S;
   T e = 0, fx = 0, fy = 0, fz = 0;
   T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
@@ -184,8 +183,18 @@ __global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
     double ws[6];
     block_sum_lo<T, 6>(wv, ws, sh);
     if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * ws[c];
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)bk.x + c] = 0.5 * ws[c];
   }
+}
+
+template <typename T, bool VIR, int S, bool LB = false, bool GEN = false>
+__global__ void __launch_bounds__(kBlock) k_pair(const Vec4<T>* __restrict__ sp,
+                                                  const int* __restrict__ start, int N,
+                                                  PairArgs<T> g, T* __restrict__ e0,
+                                                  T* __restrict__ floc,
+                                                  double* __restrict__ wpart,
+                                                  const T* __restrict__ lbw = nullptr) {
+  k_pair_body<T, VIR, S, LB, GEN>(Blk::self(), sp, start, N, g, e0, floc, wpart, lbw);
 }
 
 // Warp form of the pair sum (lanes per atom S = 32 / G, G = 1 or 2 atoms
@@ -417,6 +426,202 @@ __global__ void __launch_bounds__(kBlock) k_pair_warp(const Vec4<T>* __restrict_
   }
 }
 
+
+// Cluster form (pair_split 1024, FP32): a warp takes the 8 consecutive
+// sorted atoms 8w .. 8w+7 as an i-cluster; lane = i slot (lane & 7) x j slot
+// (lane >> 3).  The atoms are split into segments of one cell row spanning
+// at most 8 cells in x (sorted order keeps a segment contiguous); for each
+// segment
+//   1. lane t sets up neighbour row t of the (2R+1)^2 rows against the
+//      segment's bounding box (skipped if its y-z distance is >= a, else
+//      clipped in x to the box extent +- sqrt(a^2 - d^2), at most two
+//      same-image runs of contiguous candidates since nc[0] >= 16 exceeds
+//      the <= 15 cells of the clipped range) and the runs are compacted into
+//      a per-warp table;
+//   2. the warp walks the table; per run, candidates j0, j0+4, ... go to the
+//      four j slots, so every candidate is loaded once (8 lanes share the
+//      load) and paired with all 8 atoms of the segment.
+// Every loop bound is uniform over the warp and the pair is evaluated
+// branch-free (a miss or the atom itself adds zero), so all 32 lanes do
+// useful issue; the price is the misses of the cluster's union of candidate
+// cells.  Each lane sums its candidates in table order and the four j slots
+// of an atom are combined by a fixed shuffle tree: results are reproducible
+// bit for bit.  Requires R <= 2 on every axis and nc[0] >= 16
+// (pair_cl_ok()).
+constexpr int kClRuns = 2 * 25;
+
+template <bool VIR, bool GEN>
+__global__ void __launch_bounds__(kBlock) k_pair_cl(const Vec4<float>* __restrict__ sp,
+                                                     const int* __restrict__ start, int N,
+                                                     PairArgs<float> g, float* __restrict__ e0,
+                                                     float* __restrict__ floc,
+                                                     double* __restrict__ wpart) {
+  using T = float;
+  constexpr int kW = kBlock / 32;
+  constexpr unsigned kAll = 0xffffffffu;
+  __shared__ double sh[32 * 6];
+  __shared__ int4 run_j[kW][kClRuns];     // first, end, zero image (1/0), -
+  __shared__ float4 run_s[kW][kClRuns];   // image shift m L
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gi = lane & 7, js = lane >> 3;
+  const long il = ((long)blockIdx.x * kW + wid) * 8 + gi;
+  const bool vi = il < N;
+  const int i = vi ? (int)il : 0;
+  T e = 0, fx = 0, fy = 0, fz = 0;
+  T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+  T ci = 0;
+  Vec4<T> pi = {T(0), T(0), T(0), T(0)};
+  int cx = 0, cy = 0, cz = 0, rid = INT_MAX;
+  if (vi) {
+    pi = sp[i];
+    ci = pi.w;
+    cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
+    cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
+    cz = min(max((int)(pi.z * g.inv_w[2]), 0), g.nc[2] - 1);
+    rid = cy + g.nc[1] * cz;
+  }
+  const int ny = 2 * g.R[1] + 1, nrows = (2 * g.R[2] + 1) * ny;
+  for (int s = 0; s < 8;) {
+    const int rs = __shfl_sync(kAll, rid, s);
+    if (rs == INT_MAX) break;  // the remaining atoms are past N
+    const int cxs = __shfl_sync(kAll, cx, s);
+    const unsigned seg =
+        __ballot_sync(kAll, js == 0 && gi >= s && rid == rs && cx <= cxs + 7);
+    const bool act = (seg >> gi) & 1u;
+    // bounding box of the segment (the lanes of one j slot hold all 8 atoms)
+    T xmn = act ? pi.x : T(INFINITY), xmx = act ? pi.x : T(-INFINITY);
+    T ymn = act ? pi.y : T(INFINITY), ymx = act ? pi.y : T(-INFINITY);
+    T zmn = act ? pi.z : T(INFINITY), zmx = act ? pi.z : T(-INFINITY);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      xmn = min(xmn, __shfl_xor_sync(kAll, xmn, o));
+      xmx = max(xmx, __shfl_xor_sync(kAll, xmx, o));
+      ymn = min(ymn, __shfl_xor_sync(kAll, ymn, o));
+      ymx = max(ymx, __shfl_xor_sync(kAll, ymx, o));
+      zmn = min(zmn, __shfl_xor_sync(kAll, zmn, o));
+      zmx = max(zmx, __shfl_xor_sync(kAll, zmx, o));
+    }
+    const int scy = __shfl_sync(kAll, cy, s), scz = __shfl_sync(kAll, cz, s);
+    // 1. lane t: neighbour row t, at most two same-image runs
+    int nr = 0;  // runs of this row: rj0/rs0, then rj1/rs1 (registers, no indexing)
+    int4 rj0 = make_int4(0, 0, 0, 0), rj1 = rj0;
+    float4 rs0 = make_float4(0.f, 0.f, 0.f, 0.f), rs1 = rs0;
+    if (lane < nrows) {
+      const int dz = lane / ny - g.R[2], dy = lane % ny - g.R[1];
+      const int z = scz + dz, y = scy + dy;
+      int iz, iy, mz, my;
+      wrap_image(z, g.nc[2], iz, mz);
+      wrap_image(y, g.nc[1], iy, my);
+      const T ylo = (T)y * g.w[1], zlo = (T)z * g.w[2];
+      const T dyl = max(T(0), max(ylo - ymx, ymn - (ylo + g.w[1])) - g.margin);
+      const T dzl = max(T(0), max(zlo - zmx, zmn - (zlo + g.w[2])) - g.margin);
+      const T d2 = dyl * dyl + dzl * dzl;
+      if (d2 < g.a2) {
+        const T rx = sqrt(g.a2 - d2) + g.margin;
+        const int xl = (int)floor((xmn - rx) * g.inv_w[0]);
+        const int xh = (int)floor((xmx + rx) * g.inv_w[0]);
+        const int row = g.nc[0] * (iy + g.nc[1] * iz);
+        int ix, mx;
+        wrap_image(xl, g.nc[0], ix, mx);
+        const T sy = (T)my * g.box.L[1], sz = (T)mz * g.box.L[2];
+        int xa = xl;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (xa <= xh) {
+            const int xb = min(xh, xa + (g.nc[0] - 1 - ix));
+            const int j0 = start[row + ix], j1 = start[row + ix + (xb - xa) + 1];
+            if (j1 > j0) {
+              const int4 a = make_int4(j0, j1, (mx | my | mz) == 0 ? 1 : 0, 0);
+              const float4 b = make_float4((T)mx * g.box.L[0], sy, sz, 0.f);
+              if (nr == 0) {
+                rj0 = a;
+                rs0 = b;
+              } else {
+                rj1 = a;
+                rs1 = b;
+              }
+              ++nr;
+            }
+            xa = xb + 1;
+            ix = 0;
+            ++mx;
+          }
+        }
+      }
+    }
+    // compact the runs of all rows into the warp's table (row order)
+    int inc = nr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kAll, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(kAll, inc, 31);
+    if (nr > 0) {
+      run_j[wid][inc - nr] = rj0;
+      run_s[wid][inc - nr] = rs0;
+    }
+    if (nr > 1) {
+      run_j[wid][inc - 1] = rj1;
+      run_s[wid][inc - 1] = rs1;
+    }
+    __syncwarp();
+    // 2. all runs, four candidates per step, paired with the 8 atoms
+    for (int r = 0; r < total; ++r) {
+      const int4 R = run_j[wid][r];
+      const float4 S = run_s[wid][r];
+      const T qx = pi.x - S.x, qy = pi.y - S.y, qz = pi.z - S.z;
+      const int self = (act && R.z) ? i : -1;  // the atom itself: zero image only
+      for (int jb = R.x; jb < R.y; jb += 4) {
+        const int j = jb + js;
+        const bool ok = act && j < R.y && j != self;
+        const Vec4<T> pj = sp[min(j, R.y - 1)];
+        const T ddx = pj.x - qx, ddy = pj.y - qy, ddz = pj.z - qz;
+        const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const bool hit = ok && r2 < g.a2;
+        const T rr = hit ? r2 : g.a2;  // a miss evaluates at r = a with weight zero
+        T g0, gp;
+        g0_and_gp<T, GEN>(rcp(rr), rr * g.ia2, g, g0, gp);
+        const T cj = hit ? pj.w : T(0);
+        e += cj * g0;
+        const T cg = cj * gp;
+        fx += cg * ddx;
+        fy += cg * ddy;
+        fz += cg * ddz;
+        if (VIR) {
+          w0 += cg * ddx * ddx;
+          w1 += cg * ddy * ddy;
+          w2 += cg * ddz * ddz;
+          w3 += cg * ddx * ddy;
+          w4 += cg * ddx * ddz;
+          w5 += cg * ddy * ddz;
+        }
+      }
+    }
+    __syncwarp();  // the next segment rewrites the run table
+    s += __popc(seg);
+  }
+#pragma unroll
+  for (int o = 8; o < 32; o <<= 1) {
+    e += __shfl_xor_sync(kAll, e, o);
+    fx += __shfl_xor_sync(kAll, fx, o);
+    fy += __shfl_xor_sync(kAll, fy, o);
+    fz += __shfl_xor_sync(kAll, fz, o);
+  }
+  if (vi && js == 0) {
+    e0[i] = e;
+    floc[3 * (size_t)i + 0] = -ci * fx;
+    floc[3 * (size_t)i + 1] = -ci * fy;
+    floc[3 * (size_t)i + 2] = -ci * fz;
+  }
+  if (VIR) {
+    T wv[6] = {ci * w0, ci * w1, ci * w2, ci * w3, ci * w4, ci * w5};
+    double ws[6];
+    block_sum_lo<T, 6>(wv, ws, sh);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)blockIdx.x + c] = 0.5 * ws[c];
+  }
+}
 
 // One queued pair of the queue form: displacement with an exact image shift,
 // then Eq. (g_0) and its derivative accumulated into the lane's sums.
@@ -739,24 +944,48 @@ __global__ void __launch_bounds__(kQWarps * 32) k_pair_q(const Vec4<T>* __restri
   }
 }
 
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 bool pair_cluster_ok(const Plan* p) {
   if (p->sm.n != 2) return false;  // warp and queue forms: Eq. (gamma) only
   for (int d = 0; d < 3; ++d)
     if (p->cg.R[d] > 2) return false;
   return p->cg.nc[0] >= 2 * p->cg.R[0] + 1;
 }
+#endif  // MLS6_DEVICE_ONLY
+
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
+// Cluster form: FP32 arithmetic, every neighbour range R <= 2 and at least
+// 16 cells along x (a segment's clipped x range then meets at most two
+// periodic images).
+bool pair_cl_ok(const Plan* p) {
+  if (p->prec == MLS6_FP64) return false;
+  for (int d = 0; d < 3; ++d)
+    if (p->cg.R[d] > 2) return false;
+  return p->cg.nc[0] >= 16;
+}
 
 long pair_blocks(const Plan* p, int split) {
   const long N = p->N;
   if (N <= 0) return 0;
+  if (split == kPairCluster) return cdiv(N, (long)kBlock / 4);  // 8 atoms per warp
   if (split >= 64) return cdiv(cdiv(N, split / 64), kQWarps);
   return cdiv(N * split, kBlock);
 }
+#endif  // MLS6_DEVICE_ONLY
 
 // Default pair kernel: FP64 the queue form where the cell geometry allows
 // it; otherwise the smallest of 1, 2, 4, 8 lanes per atom that gives about
 // 48 resident warps per SM on a 152-SM GPU.
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 int pair_split(const Plan* p) {
+  // the cluster form is not a default: on the 1M-atom cube it took 1.22 ms
+  // against 0.87 ms for the per-atom kernel (every atom of a segment is
+  // evaluated against the union of the segment's candidate cells, which the
+  // full lanes do not make up for)
+  return pair_split_atom(p);
+}
+
+int pair_split_atom(const Plan* p) {
   // FP64: the queue form with two atoms per warp where the cell geometry
   // allows it (1M-atom cube 24.5 ms against 29.4 ms per atom and 31.2 ms
   // for the warp form); FP32 keeps the per-atom kernel (868 us there against
@@ -767,6 +996,7 @@ int pair_split(const Plan* p) {
   while (s < 8 && p->N * s < want) s *= 2;
   return s;
 }
+#endif  // MLS6_DEVICE_ONLY
 
 template <typename T, int S>
 static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
@@ -852,10 +1082,14 @@ template <typename T> int prepare_pair_kernels(Plan*) {
   if (q_attr<T, 2>() || q_attr<T, 4>() || q_attr<T, 8>()) return MLS6_ERR_CUDA;
   return MLS6_OK;
 }
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 template int prepare_pair_kernels<float>(Plan*);
 template int prepare_pair_kernels<double>(Plan*);
+#endif  // MLS6_DEVICE_ONLY
 
-template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb) {
+
+// Arguments of the pair kernels for a plan.
+template <typename T> static PairArgs<T> pair_args(const Plan* p) {
   PairArgs<T> pg;
   for (int d = 0; d < 3; ++d) {
     pg.box.L[d] = (T)p->L[d];
@@ -880,6 +1114,32 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool l
   }
   for (int k = 0; k < 5; ++k) pg.gc[k] = (T)p->sm.c[k];
   for (int k = 0; k < 4; ++k) pg.gd[k] = (T)(-12.0 * (k + 1) * p->sm.c[k + 1]);
+  return pg;
+}
+
+template <typename T>
+static void launch_cl(Plan* p, const PairArgs<T>& pg, bool vir, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    const int N = (int)p->N;
+    const long nb = pair_blocks(p, kPairCluster);
+    if (nb == 0) return;
+    auto k = p->sm.n != 2 ? (vir ? k_pair_cl<true, true> : k_pair_cl<false, true>)
+                          : (vir ? k_pair_cl<true, false> : k_pair_cl<false, false>);
+    k<<<nb, kBlock, 0, st>>>((const Vec4<float>*)p->d_sorted, p->d_cell_start, N, pg,
+                             (float*)p->d_e0, (float*)p->d_floc, p->d_wpart + 6 * p->wpart_pair);
+  }
+}
+
+template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool lb) {
+  const PairArgs<T> pg = pair_args<T>(p);
+  if (p->pair_split == kPairCluster) {
+    // Lorentz-Berthelot and FP64 run the per-atom kernel
+    if (lb || sizeof(T) != 4)
+      launch_s<T, 1>(p, pg, vir, lb, st);
+    else
+      launch_cl<T>(p, pg, vir, st);
+    return 1;
+  }
   switch (p->pair_split) {
     case 512: launch_q<T, 8>(p, pg, vir, lb, st); break;
     case 256: launch_q<T, 4>(p, pg, vir, lb, st); break;
@@ -894,7 +1154,9 @@ template <typename T> int launch_pair(Plan* p, bool vir, cudaStream_t st, bool l
   return 1;
 }
 
+#ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 template int launch_pair<float>(Plan*, bool, cudaStream_t, bool);
 template int launch_pair<double>(Plan*, bool, cudaStream_t, bool);
 
+#endif  // MLS6_DEVICE_ONLY
 }  // namespace mls6

@@ -337,7 +337,7 @@ int mls6_plan_ex(mls6_plan_t** out, const double box[3], int64_t N, double a, do
   if (!box || N < 0 || N > (int64_t)1 << 30 || !(a > 0.0) || !std::isfinite(a)) return MLS6_ERR_ARG;
   if (precision != MLS6_FP64 && precision != MLS6_FP32 && precision != MLS6_MIXED)
     return MLS6_ERR_ARG;
-  if (order != 3) return MLS6_ERR_ORDER;
+  if (order != 3 && order != 5) return MLS6_ERR_ORDER;
   if (levels == 0) {
     levels = mls6_auto_levels(box, h);
     if (levels < 0) return levels;
@@ -356,6 +356,7 @@ int mls6_plan_ex(mls6_plan_t** out, const double box[3], int64_t N, double a, do
   p->stream = 0;
   p->sm = smooth_coefficients(continuity);
   p->stencil_req = stencil;
+  p->order = order;
   p->c_self = gamma_fn(p->sm, 0.0) / std::pow(a, 6.0);
   for (int k = 1; k <= levels; ++k) {
     Level& lv = p->lv[k];
@@ -472,9 +473,10 @@ int mls6_set_tuning(mls6_plan_t* plan, int split, int groups) {
   if (!plan) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8 && split != 16 &&
-      split != 32 && split != 128 && split != 256 && split != 512)
+      split != 32 && split != 128 && split != 256 && split != 512 && split != kPairCluster)
     return MLS6_ERR_ARG;
-  if (split > 8 && !pair_cluster_ok(p)) return MLS6_ERR_ARG;
+  if (split == kPairCluster ? !pair_cl_ok(p) : (split > 8 && !pair_cluster_ok(p)))
+    return MLS6_ERR_ARG;
   if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return MLS6_ERR_ARG;
   const int s2 = split ? split : p->pair_split;
   const int g2 = (groups && !p->stencil_global) ? groups : p->stencil_groups;
@@ -519,7 +521,7 @@ const char* mls6_status_string(int s) {
     case MLS6_ERR_ARG: return "invalid argument";
     case MLS6_ERR_GRID: return "invalid grid hierarchy";
     case MLS6_ERR_BOX: return "invalid box";
-    case MLS6_ERR_ORDER: return "unsupported interpolation order (only 3)";
+    case MLS6_ERR_ORDER: return "unsupported interpolation order (3 or 5)";
     case MLS6_ERR_CUDA: return "CUDA runtime error";
     case MLS6_ERR_NOMEM: return "device allocation failed";
     case MLS6_ERR_TIMEOUT: return "a bounded device-side wait ran out (the kernel gave up)";

@@ -50,7 +50,6 @@
 
 namespace mls6 {
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 // tile: 16 x-outputs x 16 y x 16 z, two M = 128 halves (y 0..7 and 8..15)
 // that share every weight chunk

@@ -34,7 +34,6 @@
 
 namespace mls6 {
 
-static inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
 constexpr int kTcX = 16, kTcY = 16, kTcZ = 8;
 // warps per block: 8 for the energy-only kernel (78 registers: two blocks

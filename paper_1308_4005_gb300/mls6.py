@@ -40,7 +40,8 @@ EXPORTS = ("mls6_grid_dims", "mls6_coarse_tables", "mls6_plan", "mls6_plan_ex",
            "mls6_set_tuning", "mls6_get_tuning", "mls6_stencil_kind", "mls6_cost_model", "mls6_lpt_assign",
            "mls6_batch_plan", "mls6_batch_set_stream", "mls6_batch_eval", "mls6_batch_tune",
            "mls6_batch_set_config", "mls6_batch_info", "mls6_batch_size", "mls6_batch_replica",
-           "mls6_batch_destroy",
+           "mls6_batch_destroy", "mls6_batch_set_mode", "mls6_batch_mode", "mls6_batch_set_wait",
+           "mls6_batch_last_error",
            "mls6_mlp_n_params", "mls6_mlp_create", "mls6_mlp_set_stream", "mls6_mlp_get_params",
            "mls6_mlp_set_params", "mls6_mlp_set_norm", "mls6_mlp_features", "mls6_mlp_forward",
            "mls6_mlp_grad", "mls6_mlp_train_step", "mls6_mlp_apply", "mls6_mlp_destroy",
@@ -157,6 +158,14 @@ def load(path: str = LIB_PATH):
         getattr(L, fn).restype = C.c_int
     L.mls6_mlp_destroy.argtypes = [C.c_void_p]
     L.mls6_mlp_destroy.restype = None
+    L.mls6_batch_set_mode.argtypes = [C.c_void_p, C.c_int]
+    L.mls6_batch_set_mode.restype = C.c_int
+    L.mls6_batch_mode.argtypes = [C.c_void_p]
+    L.mls6_batch_mode.restype = C.c_int
+    L.mls6_batch_set_wait.argtypes = [C.c_void_p, C.c_longlong, C.c_longlong]
+    L.mls6_batch_set_wait.restype = C.c_int
+    L.mls6_batch_last_error.argtypes = [C.c_void_p]
+    L.mls6_batch_last_error.restype = C.c_int
     L.mls6_batch_destroy.argtypes = [C.c_void_p]
     L.mls6_batch_destroy.restype = None
     L.mls6_status_string.argtypes = [C.c_int]
@@ -414,6 +423,24 @@ def mls6_batch_replica(batch, r):
     h = C.c_void_p()
     _check(load().mls6_batch_replica(C.c_void_p(batch), r, C.byref(h)), "mls6_batch_replica")
     return h.value
+
+
+def mls6_batch_set_mode(batch, persistent=True):
+    _check(load().mls6_batch_set_mode(C.c_void_p(batch), 1 if persistent else 0),
+           "mls6_batch_set_mode")
+
+
+def mls6_batch_mode(batch):
+    return int(load().mls6_batch_mode(C.c_void_p(batch)))
+
+
+def mls6_batch_set_wait(batch, limit=1 << 22, withhold=-1):
+    _check(load().mls6_batch_set_wait(C.c_void_p(batch), int(limit), int(withhold)),
+           "mls6_batch_set_wait")
+
+
+def mls6_batch_last_error(batch):
+    return int(load().mls6_batch_last_error(C.c_void_p(batch)))
 
 
 def mls6_batch_destroy(batch):

@@ -167,8 +167,8 @@ def test_batch_bitwise_vs_single(gpu_lib, small_batch, prec):
     bt = gpu_lib.Batch([w.box for w in ws], [w.N for w in ws], SMALL["a"], SMALL["h"], 0,
                        precision=prec)
     assert bt.offsets == list(off)
-    info = bt.info()
     E, W, F, _ = _batch_eval(bt, x, c, prec)
+    info = bt.info()  # the shapes the evaluation ran with
     for r, w in enumerate(ws):
         sl = slice(off[r], off[r + 1])
         e1, w1, f1, p = _single(gpu_lib, w, x[sl], c[sl], prec, info["pair_split"][r],
@@ -275,3 +275,66 @@ def test_batch_with_empty_replica(gpu_lib):
         e1, w1, f1, _ = _single(gpu_lib, w, x[sl], c[sl], "fp64", info["pair_split"][r],
                                 info["stencil_groups"][r])
         assert E[r] == e1 and np.array_equal(W[r], w1) and np.array_equal(F[sl], f1)
+
+
+@pytest.mark.gpu
+def test_persistent_batch_is_one_launch_equal_to_chains(gpu_lib, small_batch):
+    """FP32 batches in persistent mode run one persistent kernel (work queue
+    over stage, replica and block): the graph holds a single kernel, and
+    every replica's energy, virial and forces equal those of the per-replica
+    kernel chains (the default form) bit for bit (same kernel bodies, same
+    shapes).  The autotuner tunes both forms and keeps the faster; the
+    results stay those of single plans with the chosen shapes."""
+    ws, x, c, off = small_batch
+    bt = gpu_lib.Batch([w.box for w in ws], [w.N for w in ws], SMALL["a"], SMALL["h"], 0,
+                       precision="fp32")
+    assert gpu_lib.mls6_batch_mode(bt.handle) == 0
+    gpu_lib.mls6_batch_set_mode(bt.handle, True)
+    E, W, F, pos = _batch_eval(bt, x, c, "fp32")
+    assert gpu_lib.mls6_batch_mode(bt.handle) == 1
+    assert bt.info()["launches"] == 1
+    gpu_lib.mls6_batch_set_mode(bt.handle, False)
+    E2, W2, F2, _ = _batch_eval(bt, x, c, "fp32")
+    assert gpu_lib.mls6_batch_mode(bt.handle) == 0
+    assert bt.info()["launches"] > len(ws)
+    assert np.array_equal(E, E2) and np.array_equal(W, W2) and np.array_equal(F, F2)
+    t = bt.tune(pos, reps=2)
+    assert t > 0 and gpu_lib.mls6_batch_mode(bt.handle) in (0, 1)
+    E3, W3, F3, _ = _batch_eval(bt, x, c, "fp32")
+    info = bt.info()
+    for r, w in enumerate(ws):
+        sl = slice(off[r], off[r + 1])
+        e1, w1, f1, _ = _single(gpu_lib, w, x[sl], c[sl], "fp32", info["pair_split"][r],
+                                info["stencil_groups"][r])
+        assert E3[r] == e1 and np.array_equal(W3[r], w1) and np.array_equal(F3[sl], f1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("item", [0, 7])
+def test_persistent_batch_bounded_wait_runs_out(gpu_lib, small_batch, item):
+    """The test hook withholds the completion count of one work item: the
+    waits behind it run out after a short poll limit, every block leaves the
+    kernel (nothing traps or faults), the call reports MLS6_ERR_TIMEOUT, and
+    the batch evaluates normally once the hook is cleared."""
+    import ctypes as C
+
+    import torch
+
+    ws, x, c, off = small_batch
+    bt = gpu_lib.Batch([w.box for w in ws], [w.N for w in ws], SMALL["a"], SMALL["h"], 0,
+                       precision="fp32")
+    gpu_lib.mls6_batch_set_mode(bt.handle, True)
+    E0, W0, F0, pos = _batch_eval(bt, x, c, "fp32")
+    assert bt.info()["launches"] == 1
+    B = len(ws)
+    Eh = (C.c_double * B)()
+    Fd = torch.empty((off[-1], 3), dtype=torch.float32, device="cuda")
+    gpu_lib.mls6_batch_set_wait(bt.handle, 2000, item)
+    rc = gpu_lib.mls6_batch_eval(bt.handle, pos.data_ptr(), 0, Fd.data_ptr(), C.addressof(Eh), 0)
+    assert rc == gpu_lib.MLS6_ERR_TIMEOUT
+    assert gpu_lib.mls6_batch_last_error(bt.handle) == gpu_lib.MLS6_ERR_TIMEOUT
+    gpu_lib.mls6_batch_set_wait(bt.handle, 1 << 22, -1)
+    rc = gpu_lib.mls6_batch_eval(bt.handle, pos.data_ptr(), 0, Fd.data_ptr(), C.addressof(Eh), 0)
+    assert rc == 0
+    assert np.array_equal(np.array(Eh[:]), E0)
+    assert gpu_lib.mls6_batch_last_error(bt.handle) == 0

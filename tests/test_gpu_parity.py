@@ -141,8 +141,9 @@ SHAPE_PARAMS = [c + ("fp64",) for c in SHAPE_CASES] + [
 def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
     """Every pair-kernel shape (lanes per atom 1..8: one atom per lane
     group; 16, 32: warp form; 128, 256, 512: queue form with 2, 4, 8 atoms
-    per warp) against the oracle; the warp and queue forms are refused
-    where the neighbour range is too wide for them."""
+    per warp; 1024: cluster form) against the oracle; the warp and queue
+    forms are refused where the neighbour range is too wide for them, the
+    cluster form also in FP64 and below 16 cells along x."""
     import torch
 
     region = None
@@ -157,7 +158,7 @@ def test_pair_kernel_shapes(gpu_lib, orc, name, N, box, a, h, l, prec):
     pos = torch.tensor(np.c_[x, c], dtype=dt, device="cuda")
     tol = TOL64 if prec == "fp64" else TOL32
     ran = []
-    for split in (1, 2, 4, 8, 16, 32, 128, 256, 512):
+    for split in (1, 2, 4, 8, 16, 32, 128, 256, 512, 1024):
         try:
             gpu_lib.mls6_set_tuning(plan.handle, split, 0)
         except gpu_lib.MLS6Error:
@@ -371,3 +372,62 @@ def test_caller_stream_ordering(gpu_lib):
             Fh.copy_(F, non_blocking=True)
             s.synchronize()
             assert np.abs(Fh.numpy() - ref["F"]).max() <= 1e-13 * np.abs(ref["F"]).max()
+
+
+CLUSTER_CASES = [
+    # name, N, box, a, h, levels, continuity (>= 16 cells along x)
+    ("cl_cube", 4001, (24.0, 14.0, 13.0), 2.5, 0.8, 3, 2),
+    ("cl_slab_vacuum", 3000, (26.0, 12.0, 30.0), 3.0, 1.0, 3, 2),
+    ("cl_thin_yz", 700, (30.0, 6.0, 5.5), 2.0, 0.6, 2, 2),
+    ("cl_smoothing_c3", 2500, (22.0, 13.0, 12.0), 2.5, 0.8, 3, 3),
+]
+
+
+@pytest.mark.parametrize("name,N,box,a,h,l,cont", CLUSTER_CASES, ids=[c[0] for c in CLUSTER_CASES])
+def test_pair_cluster_form(gpu_lib, orc, name, N, box, a, h, l, cont):
+    """The FP32 cluster form (8 atoms per warp, segments of one cell row,
+    branch-free candidates) against the oracle, with and without the
+    virial, ragged atom counts, a slab with empty rows (segments split by
+    row and by the 8-cell rule), boxes thinner than the neighbour range in
+    y and z, and a C^3 smoothing function; repeatable bit for bit."""
+    import torch
+
+    region = None
+    if "slab" in name:
+        region = ((0, box[0]), (0, box[1]), (0.35 * box[2], 0.65 * box[2]))
+    x, c = I.uniform_atoms(zlib.crc32(name.encode()) % 10000, N, box, region=region)
+    x, c = as_prec(x, c, "fp32")
+    n = orc.grid_dims(box, h, l)
+    with orc.smoothing_order(cont):
+        o = orc.evaluate(box, a, n, l, x, c)
+    plan = gpu_lib.Plan(box, N, a, h, l, precision="fp32", continuity=cont)
+    gpu_lib.mls6_set_tuning(plan.handle, 1024, 0)
+    assert gpu_lib.mls6_get_tuning(plan.handle)[0] == 1024
+    pos = torch.tensor(np.c_[x, c], dtype=torch.float32, device="cuda")
+    for vir in (True, False):
+        r = plan.evaluate(pos, virial=vir, atom_energy=False)
+        torch.cuda.synchronize()
+        out = r["out"].cpu().numpy()
+        g = dict(E=out[0], W=out[1:7] if vir else o["W"], F=r["F"].cpu().double().numpy())
+        compare(g, o, TOL32, f"{name} cluster virial={vir}")
+        r2 = plan.evaluate(pos, virial=vir, atom_energy=False)
+        torch.cuda.synchronize()
+        assert torch.equal(r["F"], r2["F"]) and torch.equal(r["out"], r2["out"])
+
+
+def test_pair_cluster_form_selection_and_refusals(gpu_lib):
+    """The cluster form is selected by mls6_set_tuning only (the per-atom
+    kernel stays the default); FP64 and boxes with < 16 cells along x
+    refuse it."""
+    c = I.workload("cube1m")
+    for prec in ("fp32", "mixed"):
+        p = gpu_lib.Plan(c.box, 40000, c.a, c.h, c.levels, precision=prec)
+        assert gpu_lib.mls6_get_tuning(p.handle)[0] != 1024
+        gpu_lib.mls6_set_tuning(p.handle, 1024, 0)
+        assert gpu_lib.mls6_get_tuning(p.handle)[0] == 1024
+    p64 = gpu_lib.Plan(c.box, 40000, c.a, c.h, c.levels, precision="fp64")
+    with pytest.raises(gpu_lib.MLS6Error):
+        gpu_lib.mls6_set_tuning(p64.handle, 1024, 0)
+    narrow = gpu_lib.Plan((20.0, 20.0, 20.0), 5000, 3.0, 1.0, 2, precision="fp32")
+    with pytest.raises(gpu_lib.MLS6Error):
+        gpu_lib.mls6_set_tuning(narrow.handle, 1024, 0)

@@ -162,7 +162,10 @@ def test_training_lowers_loss(gpu_lib, mlp_ref):
 @pytest.mark.gpu
 def test_learned_correction_gain(gpu_lib):
     """Trained on two slabs, evaluated on a held-out one: the correction
-    lowers eps_F of the h = 2 grid."""
+    closes at least a fifth of the gap between the h = 2 grid's eps_F and
+    the h = 1 grid's (measured on GB300: about a third, 3.9e-4 -> 3.5e-4
+    against 2.75e-4), and never reaches below the fine grid it learned
+    from by more than rounding."""
     from paper_1308_4005_gb300 import learn
 
     st = learn.Setup()
@@ -172,4 +175,7 @@ def test_learned_correction_gain(gpu_lib):
     box, x, c = learn.slab_system(12000, 2000)
     acc = learn.accuracy(model, st, box, x, c)
     print("eps_F", acc)
-    assert acc["learned"] < acc["coarse"]
+    gap = acc["coarse"] - acc["fine"]
+    assert gap > 0
+    assert acc["learned"] <= acc["coarse"] - 0.2 * gap, acc
+    assert acc["learned"] >= 0.9 * acc["fine"], acc
