@@ -52,7 +52,10 @@ EXACT_R = 20.0          # radius of the direct sums behind the exact sampled for
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu
 # capture on the named workload and precision (virial on); a kernel changed
 # since its capture has no entry and reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("cube1m", "mixed", "pair"): 18241536 + 256,   # k_pair<float,1,1>: sorted atoms + cell starts
+    ("cube1m", "mixed", "stencil"): 8267520 + 0,  # k_stencil_mma<1>: q of levels 1-4, B matrices
+}
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}

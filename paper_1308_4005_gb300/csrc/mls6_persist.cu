@@ -233,7 +233,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 template <bool VIR>
-__global__ void __launch_bounds__(kStencilThreads * 2, 3) k_persist(PExecArgs X) {
+__global__ void __launch_bounds__(kStencilThreads * 2) k_persist(PExecArgs X) {
   __shared__ long long s_t;
   __shared__ int s_go, s_lo;
   for (;;) {
