@@ -54,7 +54,6 @@ EXACT_R = 20.0          # radius of the direct sums behind the exact sampled for
 # since its capture has no entry and reports null.
 TRAFFIC = {
     ("cube1m", "mixed", "pair"): 18241536 + 256,   # k_pair<float,1,1>: sorted atoms + cell starts
-    ("cube1m", "mixed", "stencil"): 8267520 + 0,  # k_stencil_mma<1>: q of levels 1-4, B matrices
 }
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)

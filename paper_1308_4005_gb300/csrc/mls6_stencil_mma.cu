@@ -8,9 +8,11 @@
 // 8..15, which share every weight chunk) and one tap row,
 //     D[line][c*16 + m] += sum_k A[line][k] B_c[k][m],
 //     A[line][k] = q(x0 - 8 + k, y + dy, z + dz),   B_c[k][m] = W_c(k - 8 - m),
-// with W_c the row's weights of channel c (zero for |dx| > R_row <= 8): one
-// M = 128, K = 32 (two steps of 16) MMA per tap row and product, D in tensor
-// memory.  The A operand of every tap row is the same staged block of q,
+// with W_c the row's weights of channel c (zero for |dx| > R_row <= 8): per
+// tap row and K step of 16 one M = 128 MMA whose B operand holds the hi and
+// the lo weight matrices side by side (N = 2 x 16 x channels, so the q_hi
+// operand is read once for both products), plus one N = 16 MMA of q_lo with
+// the energy channel's hi weights; D in tensor memory.  The A operand of every tap row is the same staged block of q,
 // addressed with a shifted start: the staged layout puts the 8 y-lines of a
 // core matrix 16 bytes apart (a shift in y moves the start by 16 B) and the
 // z-lines a fixed stride apart (a shift in z moves it by that stride), so
@@ -21,7 +23,8 @@
 // offsets; the row constants dy, dz are folded into the weights so every
 // channel accumulates over all tap rows).  After the last row the tile reads
 // D back once: e = scale * D_0 is stored and, for the virial, each channel is
-// dotted with the centre values q_mu (strain derivative, Sec. II.B reading).
+// dotted with the centre values q_mu (strain derivative, Sec. II.B reading);
+// each channel is the sum of its hi-weight and lo-weight accumulator columns.
 //
 // Products (the lo*lo term is below the split's representation error):
 // energy q_hi w_hi + q_hi w_lo + q_lo w_hi (relative error <= 3 * 2^-18 per
@@ -58,11 +61,12 @@ constexpr int kMmaThreads = 128;
 template <bool VIR> __host__ __device__ constexpr int mma_n() { return VIR ? 112 : 16; }
 // tap rows per weight chunk: 28 KB (virial) or 8 KB (energy only) per chunk
 template <bool VIR> __host__ __device__ constexpr int mma_rows_per_chunk() { return VIR ? 2 : 4; }
-// tensor-memory columns per half (the accumulators of the two halves are
-// side by side)
-template <bool VIR> __host__ __device__ constexpr int mma_tmem_cols() { return VIR ? 128 : 32; }
+// tensor-memory columns per half: 2 x mma_n (hi-weight and lo-weight
+// products), rounded to a power of two; the two halves side by side
+template <bool VIR> __host__ __device__ constexpr int mma_tmem_cols() { return VIR ? 256 : 32; }
 constexpr int kMmaStagesMax = 4;  // weight buffers in flight (fewer when shared memory is short)
-// bytes of one tap row's B matrices (hi, lo) in the core-matrix layout
+// bytes of one tap row's B matrices (per K chunk of 8: hi rows, then lo
+// rows) in the core-matrix layout
 template <bool VIR> __host__ __device__ constexpr int mma_row_bytes() {
   return 2 * 4 * mma_n<VIR>() * 16;
 }
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(kMmaThreads) k_stencil_mma(MmaArgs A,
       bulk_g2s(sB + s * CB, A.B + (size_t)c * CB, (uint32_t)CB, &bar_full[s]);
     }
   } else if (tid == 0) {  // MMA issuer
-    const uint32_t idN = mma_idesc(128, NV), id16 = mma_idesc(128, 16);
+    const uint32_t id2 = mma_idesc(128, 2 * NV), id16 = mma_idesc(128, 16);
     const uint32_t sa = su32(sA), sb = su32(sB);
     const uint32_t a_sbo = (uint32_t)(Ys * 16);
     uint32_t acc = 0;
@@ -314,18 +318,18 @@ __global__ void __launch_bounds__(kMmaThreads) k_stencil_mma(MmaArgs A,
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
           const uint32_t ak = abase + (uint32_t)(2 * ks) * a_lbo;
-          const uint32_t bk = bbase + (uint32_t)(2 * ks * NV * 16);
+          const uint32_t bk = bbase + (uint32_t)(2 * ks * 2 * NV * 16);
           const uint64_t ah = mma_sdesc(ak, a_lbo, a_sbo), al = mma_sdesc(ak + a_part, a_lbo, a_sbo);
-          const uint64_t bh = mma_sdesc(bk, NV * 16, 128);
-          const uint64_t bl = mma_sdesc(bk + 4 * NV * 16, NV * 16, 128);
+          // B: per K chunk 2 NV rows (hi then lo); the first 16 rows are the
+          // energy channel's hi weights
+          const uint64_t bb = mma_sdesc(bk, 2 * NV * 16, 128);
 #pragma unroll
           for (int hh = 0; hh < kMmaHalves; ++hh) {  // half hh: y lines 8 hh .. 8 hh + 7
             const uint32_t dt = tmem + (uint32_t)(hh * TCOLS);
             const uint64_t ahh = ah + (uint64_t)(hh * 8);  // + 8 rows x 16 B, in 16-B units
             const uint64_t alh = al + (uint64_t)(hh * 8);
-            mma_f16(dt, ahh, bh, idN, acc);  // q_hi w_hi, every channel
-            mma_f16(dt, ahh, bl, idN, 1);    // q_hi w_lo, every channel
-            mma_f16(dt, alh, bh, id16, 1);   // q_lo w_hi, energy channel
+            mma_f16(dt, ahh, bb, id2, acc);  // q_hi [w_hi | w_lo], every channel
+            mma_f16(dt, alh, bb, id16, 1);   // q_lo w_hi, energy channel
           }
           acc = 1;
         }
@@ -358,8 +362,11 @@ __global__ void __launch_bounds__(kMmaThreads) k_stencil_mma(MmaArgs A,
     const int gy = y0 + 8 * hh + (r & 7), gz = z0 + (r >> 3);
     const bool line_in = gy < n1 && gz < n2 && !aborted && done;
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(hh * TCOLS);
-    float d[16];
+    float d[16], dl[16];
     tmem_ld16(taddr, d);
+    tmem_ld16(taddr + NV, dl);  // lo-weight products
+#pragma unroll
+    for (int j = 0; j < 16; ++j) d[j] += dl[j];
     const long obase = (long)n0 * (gy + (long)n1 * gz);
     if (line_in) {
       if (x0 + 16 <= n0 && ((obase + x0) & 3) == 0) {
@@ -378,11 +385,12 @@ __global__ void __launch_bounds__(kMmaThreads) k_stencil_mma(MmaArgs A,
       for (int j = 0; j < 16; ++j) qc[j] = (line_in && x0 + j < n0) ? q[obase + x0 + j] : 0.f;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        float dc[16];
+        float dc[16], dcl[16];
         tmem_ld16(taddr + 16 * (c + 1), dc);
+        tmem_ld16(taddr + NV + 16 * (c + 1), dcl);
         float sacc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sacc += qc[j] * dc[j];
+        for (int j = 0; j < 16; ++j) sacc += qc[j] * (dc[j] + dcl[j]);
         w6[c] += sacc;
       }
     }
@@ -468,8 +476,10 @@ void stencil_mma_geometry(Plan* p) {
 }
 
 // Weight matrices in the layout of the MMA's B operand: per tap row (padded
-// to a multiple of the chunk size with zero rows), part (hi, lo), K chunk
-// (8 inputs), column n = channel * 16 + output m, 8 BF16 inputs: 16 bytes.
+// to a multiple of the chunk size with zero rows), K chunk (8 inputs), part
+// (hi, lo), column n = channel * 16 + output m, 8 BF16 inputs: 16 bytes.
+// Within a K chunk the hi rows and then the lo rows are one operand of
+// 2 NV rows.
 template <bool VIR> static std::vector<uint8_t> weight_matrices(const Plan* p, int nrows_pad) {
   constexpr int NV = mma_n<VIR>();
   std::vector<uint8_t> out((size_t)nrows_pad * mma_row_bytes<VIR>(), 0);
@@ -496,8 +506,8 @@ template <bool VIR> static std::vector<uint8_t> weight_matrices(const Plan* p, i
         const uint16_t h = bf16_bits_rn((float)w);
         const uint16_t l = bf16_bits_rn((float)(w - (double)bf16_to_float(h)));
         const int kc = k / 8, kk = k % 8;
-        row[((0 * 4 + kc) * NV + n) * 8 + kk] = h;
-        row[((1 * 4 + kc) * NV + n) * 8 + kk] = l;
+        row[((kc * 2 + 0) * NV + n) * 8 + kk] = h;
+        row[((kc * 2 + 1) * NV + n) * 8 + kk] = l;
       }
     }
   }
