@@ -53,7 +53,8 @@ EXACT_R = 20.0          # radius of the direct sums behind the exact sampled for
 # capture on the named workload and precision (virial on); a kernel changed
 # since its capture has no entry and reports null.
 TRAFFIC = {
-    ("cube1m", "mixed", "pair"): 18241536 + 256,   # k_pair<float,1,1>: sorted atoms + cell starts
+    ("cube1m", "mixed", "pair"): 18241536 + 6144,  # k_pair<float,1,1>: sorted atoms + cell starts
+    ("cube1m", "mixed", "stencil"): 8271104 + 0,   # k_stencil_mma<1>: q of levels 1-4 (+ L2 misses)
 }
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)

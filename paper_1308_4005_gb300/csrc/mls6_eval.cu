@@ -74,7 +74,7 @@ template <typename T> static int upload_tables_t(Plan* p) {
   rc |= A((void**)&p->d_cell_count, sizeof(int) * p->cg.ncell);
   rc |= A((void**)&p->d_cell_start, sizeof(int) * (p->cg.ncell + 1));
   rc |= A((void**)&p->d_scan, 2 * sizeof(int) * std::max(1L, cdiv(p->cg.ncell, kScanTile)));
-  rc |= A(&p->d_sorted, sizeof(Vec4<T>) * N);
+  rc |= A(&p->d_sorted, sizeof(Vec4<T>) * (N + 3));  // 3 padding records (pair kernel loads)
   rc |= A((void**)&p->d_sorted_idx, sizeof(int) * N);
   rc |= A(&p->d_e0, e * N);
   rc |= A(&p->d_floc, 3 * e * N);

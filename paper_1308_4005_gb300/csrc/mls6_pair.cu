@@ -122,19 +122,20 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
       for (; dx <= xhi; ix = 0, ++wx) {  // runs of one image; the next starts at cell 0
         const int last = min(xhi, dx + (g.nc[0] - 1 - ix));
         const T px = pi.x - (T)wx * g.box.L[0];
-        const bool same = (wx | my | mz) == 0;
         const int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
-        // candidates four at a time: the four loads are issued together;
-        // slots past the run (or the atom itself) are never inside a
+        // candidates four at a time: the four loads are issued together (the
+        // sorted array has three padding records, so j + u stays in bounds);
+        // slots past the run are never inside a, and the atom itself (zero
+        // image, r = 0 exactly) is excluded by r^2 > 0
         for (int j = j0; j < j1; j += 4) {
           Vec4<T> pj[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) pj[u] = sp[min(j + u, j1 - 1)];
+          for (int u = 0; u < 4; ++u) pj[u] = sp[j + u];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const T ddx = pj[u].x - px, ddy = pj[u].y - py, ddz = pj[u].z - pz;
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            const bool valid = (j + u < j1) && !(same && j + u == i);
+            const bool valid = (j + u < j1) && r2 > T(0);
             if (valid && r2 < g.a2) {
               T g0, gp;
               g0_and_gp<T, GEN>(rcp(r2), r2 * g.ia2, g, g0, gp);
