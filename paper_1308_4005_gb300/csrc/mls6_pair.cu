@@ -78,6 +78,14 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdiv
 // sigma_i in place of c_i and lbw holds sqrt(2 eps_i) in sorted order; the
 // pair coefficient is C_ij = lbw_i lbw_j ((sigma_i + sigma_j)/2)^6, and the
 // outputs are e0_i = sum_j C_ij g_0 and F_i = -sum_j C_ij g_0'/r d.
+// Virial: a pair in the zero periodic image is met from both of its atoms,
+// with d_ji = -d_ij, so its d (x) d terms over all atoms equal
+// -2 sum_i F0_i (x) x_i, F0_i = sum_j c_j g_0'/r d over atom i's zero-image
+// pairs (x_i the wrapped position the separations are taken from).  That
+// product is formed once per atom; only pairs in a shifted image (runs of
+// cells across a periodic face) add their d (x) d terms one by one.  The
+// per-atom terms are not the atom's share of the virial, but their sum over
+// all atoms is the virial.
 template <typename T, bool VIR, int S, bool LB = false, bool GEN = false>
 __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restrict__ sp,
                                                   const int* __restrict__ start, int N,
@@ -89,11 +97,15 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
   const int gid = bk.x * blockDim.x + threadIdx.x;
   const int i = gid / S, sub = gid % S;
   T e = 0, fx = 0, fy = 0, fz = 0;
-  T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-  T ci = 0, wi = 0;
+  T sfx = 0, sfy = 0, sfz = 0;  // force sum over pairs in shifted images
+  T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;  // their d (x) d terms
+  T ci = 0, wi = 0, xi = 0, yi = 0, zi = 0;
   if (i < N) {
     const Vec4<T> pi = sp[i];
     ci = pi.w;
+    xi = pi.x;
+    yi = pi.y;
+    zi = pi.z;
     if (LB) wi = lbw[i];
     const int cx = min(max((int)(pi.x * g.inv_w[0]), 0), g.nc[0] - 1);
     const int cy = min(max((int)(pi.y * g.inv_w[1]), 0), g.nc[1] - 1);
@@ -122,6 +134,7 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
       for (; dx <= xhi; ix = 0, ++wx) {  // runs of one image; the next starts at cell 0
         const int last = min(xhi, dx + (g.nc[0] - 1 - ix));
         const T px = pi.x - (T)wx * g.box.L[0];
+        const bool shifted = (wx | my | mz) != 0;
         const int j0 = start[row + ix], j1 = start[row + ix + (last - dx) + 1];
         // candidates four at a time: the four loads are issued together (the
         // sorted array has three padding records, so j + u stays in bounds);
@@ -146,16 +159,20 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
               }
               e += cj * g0;
               const T cg = cj * gp;
-              fx += cg * ddx;
-              fy += cg * ddy;
-              fz += cg * ddz;
-              if (VIR) {
-                w0 += cg * ddx * ddx;
-                w1 += cg * ddy * ddy;
-                w2 += cg * ddz * ddz;
-                w3 += cg * ddx * ddy;
-                w4 += cg * ddx * ddz;
-                w5 += cg * ddy * ddz;
+              const T cgx = cg * ddx, cgy = cg * ddy, cgz = cg * ddz;
+              fx += cgx;
+              fy += cgy;
+              fz += cgz;
+              if (VIR && shifted) {
+                sfx += cgx;
+                sfy += cgy;
+                sfz += cgz;
+                w0 += cgx * ddx;
+                w1 += cgy * ddy;
+                w2 += cgz * ddz;
+                w3 += cgx * ddy;
+                w4 += cgx * ddz;
+                w5 += cgy * ddz;
               }
             }
           }
@@ -163,6 +180,19 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
         dx = last + 1;
       }
     }
+  }
+  // virial terms of this lane, from its own partial sums (before the lanes of
+  // the atom exchange them); lanes of one atom hold disjoint candidate sets,
+  // and the zero-image term is linear in the lane's partial force sum
+  T wv[6];
+  if (VIR) {
+    const T f0x = fx - sfx, f0y = fy - sfy, f0z = fz - sfz;
+    wv[0] = ci * (w0 - T(2) * f0x * xi);
+    wv[1] = ci * (w1 - T(2) * f0y * yi);
+    wv[2] = ci * (w2 - T(2) * f0z * zi);
+    wv[3] = ci * (w3 - (f0x * yi + f0y * xi));
+    wv[4] = ci * (w4 - (f0x * zi + f0z * xi));
+    wv[5] = ci * (w5 - (f0y * zi + f0z * yi));
   }
 #pragma unroll
   for (int o = S / 2; o > 0; o >>= 1) {
@@ -179,8 +209,6 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
     floc[3 * (size_t)i + 2] = -cf * fz;
   }
   if (VIR) {
-    // lanes of one atom hold disjoint candidate sets: all contribute
-    T wv[6] = {ci * w0, ci * w1, ci * w2, ci * w3, ci * w4, ci * w5};
     double ws[6];
     block_sum_lo<T, 6>(wv, ws, sh);
     if (threadIdx.x == 0)
