@@ -74,7 +74,9 @@ typedef enum {
 
 /* Finest-grid size for a box (per axis the multiple of 2^(levels-1) nearest
  * to L/h, ties to the finer grid).  Host only; needs no GPU.
- * box: 3 doubles (Lx, Ly, Lz).  n_out: 3 ints.  Returns MLS6_OK or an error. */
+ * box: 3 doubles (Lx, Ly, Lz).  n_out: 3 ints.  Returns MLS6_OK or an error
+ * (MLS6_ERR_SIZE for a finest grid of more than 2^31 - 1 nodes, which the
+ * grid kernels cannot index; mls6_plan returns the same). */
 int mls6_grid_dims(const double box[3], double h, int levels, int n_out[3]);
 
 /* Coarsest-level periodic tables (Eqs. last-grid-periodic and

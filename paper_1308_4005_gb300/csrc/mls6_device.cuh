@@ -19,8 +19,14 @@ template <typename T> struct Box3 {
   T L[3], invL[3];
 };
 
+// i mod n in [0, n).  Indices are nearly always within one period of the
+// grid (a node's neighbours), which is tested first; the remainder is taken
+// only for grids narrower than the offset (repeated wrapping).
 __device__ __forceinline__ int wrapi(int i, int n) {
-  int m = i % n;
+  if ((unsigned)i < (unsigned)n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i - n < n) return i - n;
+  const int m = i % n;
   return m < 0 ? m + n : m;
 }
 

@@ -297,10 +297,12 @@ __device__ __forceinline__ void k_restrict_body(const Blk bk,const T* __restrict
                            int c0, int c1, int c2) {
   const long z = pdl_begin();
   qf += z;
-  long mu = (long)bk.x * blockDim.x + threadIdx.x;
-  long np = (long)c0 * c1 * c2;
+  const long mu = (long)bk.x * blockDim.x + threadIdx.x;
+  const long np = (long)c0 * c1 * c2;
   if (mu >= np) return;
-  int m0 = (int)(mu % c0), m1 = (int)((mu / c0) % c1), m2 = (int)(mu / ((long)c0 * c1));
+  const unsigned u = (unsigned)mu, uc0 = (unsigned)c0, uc1 = (unsigned)c1;  // grids < 2^31 nodes
+  const unsigned q0 = u / uc0;
+  const int m0 = (int)(u - q0 * uc0), m1 = (int)(q0 % uc1), m2 = (int)(q0 / uc1);
   constexpr int NT = NP + 1, H = NP / 2;  // taps per axis, nonzero half-integer weights
   int off[NT];
   T wt[NT];
@@ -313,16 +315,23 @@ __device__ __forceinline__ void k_restrict_body(const Blk bk,const T* __restrict
   }
   off[H] = 0;
   wt[H] = T(1);
+  int ix[NT], iy[NT], iz[NT];  // wrapped fine indices per axis
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    ix[k] = wrapi(2 * m0 + off[k], f0);
+    iy[k] = wrapi(2 * m1 + off[k], f1);
+    iz[k] = wrapi(2 * m2 + off[k], f2);
+  }
   T acc = 0;
+#pragma unroll
   for (int c = 0; c < NT; ++c) {
-    int z = wrapi(2 * m2 + off[c], f2);
+#pragma unroll
     for (int b = 0; b < NT; ++b) {
-      int y = wrapi(2 * m1 + off[b], f1);
-      long row = (long)f0 * (y + (long)f1 * z);
-      T wyz = wt[b] * wt[c];
+      const T* row = qf + (size_t)f0 * (iy[b] + (size_t)f1 * iz[c]);
       T s = 0;
-      for (int a = 0; a < NT; ++a) s += wt[a] * qf[row + wrapi(2 * m0 + off[a], f0)];
-      acc += wyz * s;
+#pragma unroll
+      for (int a = 0; a < NT; ++a) s += wt[a] * row[ix[a]];
+      acc += (wt[b] * wt[c]) * s;
     }
   }
   qc[mu] = acc;
@@ -688,10 +697,12 @@ __device__ __forceinline__ void k_prolong_body(const Blk bk,const T* __restrict_
                           T* __restrict__ etf) {
   const long z = pdl_begin();
   ef += z; etc_ += z;
-  long mu = (long)bk.x * blockDim.x + threadIdx.x;
-  long np = (long)f0 * f1 * f2;
+  const long mu = (long)bk.x * blockDim.x + threadIdx.x;
+  const long np = (long)f0 * f1 * f2;
   if (mu >= np) return;
-  int m[3] = {(int)(mu % f0), (int)((mu / f0) % f1), (int)(mu / ((long)f0 * f1))};
+  const unsigned u = (unsigned)mu, uf0 = (unsigned)f0, uf1 = (unsigned)f1;  // grids < 2^31 nodes
+  const unsigned q0 = u / uf0;
+  int m[3] = {(int)(u - q0 * uf0), (int)(q0 % uf1), (int)(q0 / uf1)};
   int nc[3] = {c0, c1, c2};
   constexpr int H = NP / 2;
   int idx[3][NP];
@@ -777,17 +788,19 @@ __device__ __forceinline__ void k_interp_body(const Blk bk,
     phid<NP>(u0 - f0, wx, dx);
     phid<NP>(u1 - f1, wy, dy);
     phid<NP>(u2 - f2, wz, dz);
-    int ix[NP];
+    int ix[NP], iy[NP], iz[NP];  // wrapped node indices per axis
 #pragma unroll
-    for (int k = 0; k < NP; ++k) ix[k] = wrapi(b0 - B0 + k, n0);
+    for (int k = 0; k < NP; ++k) {
+      ix[k] = wrapi(b0 - B0 + k, n0);
+      iy[k] = wrapi(b1 - B0 + k, n1);
+      iz[k] = wrapi(b2 - B0 + k, n2);
+    }
     T acc = 0, g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
-      int z = wrapi(b2 - B0 + c, n2);
 #pragma unroll
       for (int b = 0; b < NP; ++b) {
-        int y = wrapi(b1 - B0 + b, n1);
-        const T* row = et + (long)n0 * (y + (long)n1 * z);
+        const T* row = et + (long)n0 * (iy[b] + (long)n1 * iz[c]);
         T sx = 0, sdx = 0;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {

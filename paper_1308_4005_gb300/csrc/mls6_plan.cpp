@@ -255,6 +255,8 @@ static int grid_dims_impl(const double box[3], double h, int levels, int n_out[3
     if (pick < 1) pick = 1;
     n_out[d] = (int)(pick * m);
   }
+  // the grid kernels index nodes with 32-bit integers
+  if ((double)n_out[0] * n_out[1] * n_out[2] > 2147483647.0) return MLS6_ERR_SIZE;
   return MLS6_OK;
 }
 
