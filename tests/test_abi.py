@@ -45,6 +45,16 @@ def test_grid_dims_match_oracle(lib, orc):
         assert mls6.mls6_grid_dims(L, h, lev) == orc.grid_dims(L, h, lev)
 
 
+def test_grid_dims_refuse_grids_beyond_32_bit_node_indices(lib):
+    """The grid kernels index nodes with 32-bit integers: a finest grid of
+    more than 2^31 - 1 nodes is refused (MLS6_ERR_SIZE), one just below is
+    accepted."""
+    assert mls6.mls6_grid_dims((1290.0, 1290.0, 1290.0), 1.0, 1) == (1290, 1290, 1290)
+    with pytest.raises(mls6.MLS6Error) as e:
+        mls6.mls6_grid_dims((1291.0, 1291.0, 1291.0), 1.0, 1)
+    assert e.value.code == mls6.MLS6_ERR_SIZE
+
+
 @pytest.mark.parametrize("box,nl,l,a", [
     ((10.0, 10.0, 10.0), (3, 3, 3), 3, 2.5),
     ((40.0, 40.0, 120.0), (4, 4, 12), 4, 3.0),
