@@ -691,6 +691,28 @@ template <typename T> int launch_top(Plan* p, bool vir, cudaStream_t st) {
 // -------------------------------------------------------------- prolongation
 
 // e^{k,tot}_mu = e^k_mu + sum_nu prod_d Phi(mu_d/2 - nu_d) e^{k+1,tot}_nu.
+// Per axis an even fine index meets one coarse node (weight 1), an odd one
+// the NP coarse nodes around it (weights Phi at half-integers).
+template <typename T, int NP>
+__device__ __forceinline__ int prolong_axis(int m, int nc, int (&idx)[NP], T (&wt)[NP]) {
+  constexpr int H = NP / 2;
+  if ((m & 1) == 0) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      idx[k] = wrapi(m >> 1, nc);
+      wt[k] = k == 0 ? T(1) : T(0);
+    }
+    return 1;
+  }
+  const int h = (m - 1) >> 1;  // coarse node left of m
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {  // coarse nodes h - (H-1) .. h + H
+    idx[k] = wrapi(h - (H - 1) + k, nc);
+    wt[k] = half_weight<NP, T>(k < H ? H - 1 - k : k - H);
+  }
+  return NP;
+}
+
 template <typename T, int NP = 4>
 __device__ __forceinline__ void k_prolong_body(const Blk bk,const T* __restrict__ ef, int f0, int f1, int f2,
                           const T* __restrict__ etc_, int c0, int c1, int c2,
@@ -702,35 +724,28 @@ __device__ __forceinline__ void k_prolong_body(const Blk bk,const T* __restrict_
   if (mu >= np) return;
   const unsigned u = (unsigned)mu, uf0 = (unsigned)f0, uf1 = (unsigned)f1;  // grids < 2^31 nodes
   const unsigned q0 = u / uf0;
-  int m[3] = {(int)(u - q0 * uf0), (int)(q0 % uf1), (int)(q0 / uf1)};
-  int nc[3] = {c0, c1, c2};
-  constexpr int H = NP / 2;
-  int idx[3][NP];
-  T wt[3][NP];
-  int cnt[3];
-  for (int d = 0; d < 3; ++d) {
-    if ((m[d] & 1) == 0) {
-      cnt[d] = 1;
-      idx[d][0] = wrapi(m[d] >> 1, nc[d]);
-      wt[d][0] = T(1);
-    } else {
-      cnt[d] = NP;
-      int h = (m[d] - 1) >> 1;  // coarse node left of mu
+  int ix[NP], iy[NP], iz[NP];
+  T wx[NP], wy[NP], wz[NP];
+  const int nx = prolong_axis<T, NP>((int)(u - q0 * uf0), c0, ix, wx);
+  const int ny = prolong_axis<T, NP>((int)(q0 % uf1), c1, iy, wy);
+  const int nz = prolong_axis<T, NP>((int)(q0 / uf1), c2, iz, wz);
+  T acc = 0;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {  // coarse nodes h - (H-1) .. h + H
-        idx[d][k] = wrapi(h - (H - 1) + k, nc[d]);
-        wt[d][k] = half_weight<NP, T>(k < H ? H - 1 - k : k - H);
+  for (int c = 0; c < NP; ++c) {
+    if (c >= nz) break;
+#pragma unroll
+    for (int b = 0; b < NP; ++b) {
+      if (b >= ny) break;
+      const T* row = etc_ + (size_t)c0 * (iy[b] + (size_t)c1 * iz[c]);
+      T s = 0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (a >= nx) break;
+        s += wx[a] * row[ix[a]];
       }
+      acc += wy[b] * wz[c] * s;
     }
   }
-  T acc = 0;
-  for (int c = 0; c < cnt[2]; ++c)
-    for (int b = 0; b < cnt[1]; ++b) {
-      long row = (long)c0 * (idx[1][b] + (long)c1 * idx[2][c]);
-      T s = 0;
-      for (int a = 0; a < cnt[0]; ++a) s += wt[0][a] * etc_[row + idx[0][a]];
-      acc += wt[1][b] * wt[2][c] * s;
-    }
   etf[mu] = ef[mu] + acc;
 }
 
