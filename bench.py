@@ -49,12 +49,19 @@ TARGET_EPS = 1e-4       # equal-accuracy point of the metric
 EXACT_R = 20.0          # radius of the direct sums behind the exact sampled forces
 
 
-# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu
-# capture on the named workload and precision (virial on); a kernel changed
-# since its capture has no entry and reports null.
+# DRAM bytes (read + write) per step of each stage's kernels (all launches
+# of the stage in one evaluation, L2 flushed before the step), from one ncu
+# launch-list capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# named workload and precision, virial on; a kernel changed since its
+# capture has no entry and reports null.
 TRAFFIC = {
-    ("cube1m", "mixed", "pair"): 18241536 + 6144,  # k_pair<float,1,1>: sorted atoms + cell starts
-    ("cube1m", "mixed", "stencil"): 8271104 + 0,   # k_stencil_mma<1>: q of levels 1-4 (+ L2 misses)
+    ("cube1m", "mixed", "bin"): 84425728,          # k_bin, scans, k_scatter, k_cellsort
+    ("cube1m", "mixed", "pair"): 18244096,         # k_pair<float, 1>: sorted atoms + cell starts
+    ("cube1m", "mixed", "anterpolate"): 28061184,  # k_anterp + k_from_fixed
+    ("cube1m", "mixed", "restrict"): 6534656,      # k_restrict, 4 levels
+    ("cube1m", "mixed", "stencil"): 8270080,       # k_stencil_mma<1>: q of levels 1-4
+    ("cube1m", "mixed", "prolongate"): 7336960,    # k_prolong, 4 levels
+    ("cube1m", "mixed", "interpolate"): 45970688,  # k_interp (+ final reduction)
 }
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
