@@ -116,13 +116,29 @@ __device__ __forceinline__ void k_anterp_body(const Blk bk,
   const T f0 = floor(u0), f1 = floor(u1), f2 = floor(u2);
   const int b0 = (int)f0, b1 = (int)f1, b2 = (int)f2;
   __syncthreads();
-  if (valid) {  // bounding box of the block's supports (unwrapped node indices)
-    atomicMin(&lo[0], b0 - (NP / 2 - 1));
-    atomicMin(&lo[1], b1 - (NP / 2 - 1));
-    atomicMin(&lo[2], b2 - (NP / 2 - 1));
-    atomicMax(&hi[0], b0 + NP / 2);
-    atomicMax(&hi[1], b1 + NP / 2);
-    atomicMax(&hi[2], b2 + NP / 2);
+  {  // bounding box of the block's supports (unwrapped node indices): warp
+     // minima and maxima first, then one shared atomic per warp and axis
+    int l0 = valid ? b0 - (NP / 2 - 1) : INT_MAX, l1 = valid ? b1 - (NP / 2 - 1) : INT_MAX;
+    int l2 = valid ? b2 - (NP / 2 - 1) : INT_MAX;
+    int h0 = valid ? b0 + NP / 2 : INT_MIN, h1 = valid ? b1 + NP / 2 : INT_MIN;
+    int h2 = valid ? b2 + NP / 2 : INT_MIN;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      l0 = min(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+      l1 = min(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+      l2 = min(l2, __shfl_xor_sync(0xffffffffu, l2, o));
+      h0 = max(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+      h1 = max(h1, __shfl_xor_sync(0xffffffffu, h1, o));
+      h2 = max(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+    }
+    if ((threadIdx.x & 31) == 0 && l0 != INT_MAX) {
+      atomicMin(&lo[0], l0);
+      atomicMin(&lo[1], l1);
+      atomicMin(&lo[2], l2);
+      atomicMax(&hi[0], h0);
+      atomicMax(&hi[1], h1);
+      atomicMax(&hi[2], h2);
+    }
   }
   __syncthreads();
   const T scale = Fixed<T>::pow2(sexp);
@@ -180,10 +196,7 @@ __device__ __forceinline__ void k_anterp_body(const Blk bk,
       for (int x = lane; x < e0; x += 32) {
         const U v = br[x];
         if (v == 0) continue;
-        int ix = lo[0] + x;  // within a few nodes of [0, n0)
-        while (ix < 0) ix += n0;
-        while (ix >= n0) ix -= n0;
-        atomicAdd(&qfx[row + ix], v);
+        atomicAdd(&qfx[row + wrapi(lo[0] + x, n0)], v);
       }
     }
   }

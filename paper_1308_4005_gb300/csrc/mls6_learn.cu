@@ -134,16 +134,22 @@ __global__ void __launch_bounds__(3 * kFA) k_features(
     T e[9], gx[9], gy[9], gz[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) e[k] = gx[k] = gy[k] = gz[k] = T(0);
+    int ixw[6], iyw[6];  // wrapped x and y node indices, b - 2 .. b + 3
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      ixw[k] = wrapi(b0 - 2 + k, n0);
+      iyw[k] = wrapi(b1 - 2 + k, n1);
+    }
     for (int c = 0; c < 4; ++c) {
       const int iz = wrapi(b2 + dz - 1 + c, n2);
       // x pass: rows y = b1-2 .. b1+3, offsets dx = -1..1
       T ax[6][3], bx[6][3];
 #pragma unroll
       for (int yy = 0; yy < 6; ++yy) {
-        const T* row = E + (long)n0 * (wrapi(b1 - 2 + yy, n1) + (long)n1 * iz);
+        const T* row = E + (long)n0 * (iyw[yy] + (long)n1 * iz);
         T v[6];
 #pragma unroll
-        for (int xx = 0; xx < 6; ++xx) v[xx] = row[wrapi(b0 - 2 + xx, n0)];
+        for (int xx = 0; xx < 6; ++xx) v[xx] = row[ixw[xx]];
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
           T s = 0, ds = 0;
