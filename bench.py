@@ -286,6 +286,26 @@ def eps_F(F, Fex):
     return float(np.sqrt(np.sum((F - Fex) ** 2) / np.sum(Fex ** 2)))
 
 
+def best_at_target(points, target=TARGET_EPS):
+    """The form's throughput at eps_F = target, choosing the grid spacing:
+    at_target along the cutoff sweep of each h, the best interpolated one
+    (extrapolated ones only when no h brackets the target)."""
+    by_h = {}
+    for p in points:
+        if p.get("eps_F"):
+            by_h.setdefault(p["h"], []).append(p)
+    best = None
+    for h, pts in by_h.items():
+        r = at_target(pts, target)
+        if r["value"] is None:
+            continue
+        r = dict(r, h=h)
+        rank = (r["how"] == "interpolated", r["value"])
+        if best is None or rank > (best["how"] == "interpolated", best["value"]):
+            best = r
+    return best or {"value": None, "how": "fewer than two points"}
+
+
 def at_target(points, target=TARGET_EPS):
     """Throughput at eps_F = target by log-log interpolation between the
     bracketing points of a cutoff sweep (extrapolated from the nearest two
@@ -860,23 +880,33 @@ def run_ours(args):
             "F_exact": (f"direct periodic sum of c_i c_j r^-6 over every image within "
                         f"{EXACT_R} sigma"),
             "target": TARGET_EPS}
+        # accuracy sweep over the cutoff a and the finest spacing h (the
+        # workload's h with its levels first; coarser h with the automatic
+        # level count): each form's throughput at eps_F = 1e-4 is taken on
+        # the h that reaches it fastest (the paper trades a against h for a
+        # given accuracy, Sec. IV)
         sweep = {"fp32": [], "mixed": []}
-        for a in (3.0, 3.5, 4.0):
-            for prec in ("fp32", "mixed"):
-                try:
-                    sweep[prec].append(form_point(torch, mls6, dev, stream, flush, w, x, c, prec,
-                                                  a, w.h, w.levels, idx, Fex, 10))
-                except Exception as e:  # report, keep the main line
-                    sweep[prec].append({"a": a, "error": repr(e)})
+        for h in (w.h, 1.25 * w.h, 1.5 * w.h, 2.0 * w.h):
+            for a in (3.0, 3.5, 4.0):
+                for prec in ("fp32", "mixed"):
+                    lev = w.levels if h == w.h else 0
+                    try:
+                        sweep[prec].append(form_point(torch, mls6, dev, stream, flush, w, x, c,
+                                                      prec, a, h, lev, idx, Fex, 10))
+                    except Exception as e:  # report, keep the main line
+                        sweep[prec].append({"a": a, "h": h, "error": repr(e)})
         log(f"sweep done at {time.time() - t_start:.0f} s")
         line["forms"] = {p: dict(v[0]) for p, v in sweep.items() if v and "value" in v[0]}
         line["sweep"] = sweep
-        at = {p: at_target(v) for p, v in sweep.items()}
+        # best over h, and along the workload's own h
+        at = {p: dict(best_at_target(v),
+                      at_workload_h=at_target([q for q in v if q.get("h") == w.h]))
+              for p, v in sweep.items()}
         try:
             lp = [learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, 10, log)
                   for a in (3.0, 3.5)]
             line["learned"] = lp
-            at["learned"] = at_target(lp)
+            at["learned"] = best_at_target(lp)
         except Exception as e:
             line["learned"] = {"error": repr(e)}
         log(f"learned done at {time.time() - t_start:.0f} s")
@@ -892,7 +922,7 @@ def run_ours(args):
                               not args.no_tune) for a in (2.5, 3.5)]
             bp[0]["generate_s"] = t_gen
             line["batched"] = bp
-            at["batched"] = at_target(bp)
+            at["batched"] = best_at_target(bp)
         except Exception as e:
             line["batched"] = {"error": repr(e)}
         log(f"batched done at {time.time() - t_start:.0f} s")

@@ -44,3 +44,18 @@ def test_equal_accuracy_interpolation():
     r = bench.at_target(pts, 2e-4)  # halfway in log between 1e-4 and 4e-4
     assert r["value"] == pytest.approx(4.0 * np.sqrt(2.0))
     assert bench.at_target(pts[:2], 1e-4)["how"] == "extrapolated"
+
+
+def test_equal_accuracy_takes_the_fastest_spacing():
+    """Each form's figure at the target error is taken on the grid spacing h
+    whose cutoff sweep reaches it fastest; a bracketing (interpolated) h is
+    preferred to an extrapolated one."""
+    fine = [{"h": 1.0, "eps_F": 4e-4, "value": 8.0}, {"h": 1.0, "eps_F": 1e-4, "value": 4.0}]
+    coarse = [{"h": 2.0, "eps_F": 4e-4, "value": 12.0}, {"h": 2.0, "eps_F": 1e-4, "value": 6.0}]
+    r = bench.best_at_target(fine + coarse, 1e-4)
+    assert r["h"] == 2.0 and r["value"] == pytest.approx(6.0) and r["how"] == "interpolated"
+    # a faster but extrapolated h loses to an interpolated one
+    far = [{"h": 3.0, "eps_F": 8e-4, "value": 50.0}, {"h": 3.0, "eps_F": 4e-4, "value": 40.0}]
+    r = bench.best_at_target(fine + far, 1e-4)
+    assert r["h"] == 1.0 and r["how"] == "interpolated"
+    assert bench.best_at_target([], 1e-4)["value"] is None
