@@ -168,12 +168,18 @@ int mls6_set_graph(mls6_plan_t* p, int enable);
  * prolongation, interpolation) plus the local pair sum of Eq. (g_0), i.e.
  * the quadratic form of Eq. (pot-vec-mat-vec) with xi = c, split as in
  * Eq. (pot-initial-splitting).
- *   pos     device pointer, N rows of the plan's precision (double or float):
- *           if c == NULL each row is {x, y, z, c} (4 values), otherwise
- *           {x, y, z} (3 values).  Positions may lie anywhere; they are
- *           wrapped into the box.  Read only.
- *   c       device pointer to N coefficients c_i = sqrt(C6_i) (plan
- *           precision) or NULL (coefficients in the 4th column of pos).
+ *   pos     N rows of the plan's precision (double or float): if c == NULL
+ *           each row is {x, y, z, c} (4 values), otherwise {x, y, z}
+ *           (3 values).  Positions may lie anywhere; they are wrapped into
+ *           the box.  Read only, by the binning kernel alone: device memory,
+ *           or page-locked host memory (cudaHostAlloc, cudaMallocHost,
+ *           cudaHostRegister) that the kernel reads over the host link with
+ *           no separate copy; other host memory returns MLS6_ERR_ARG.  With
+ *           host memory the caller keeps it unchanged until the evaluation
+ *           has finished on the plan's stream.
+ *   c       N coefficients c_i = sqrt(C6_i) (plan precision), device or
+ *           page-locked host memory as pos, or NULL (coefficients in the 4th
+ *           column of pos).
  *   forces  device pointer, N x 3 of the plan precision, overwritten.
  *   energy  one double, host or device pointer, or NULL to skip.
  *   virial  six doubles (xx yy zz xy xz yz), host or device, or NULL to skip
@@ -199,9 +205,11 @@ int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces
  * xi_{i,k} = (1/8) sigma_i^k sqrt(binom(6,k) 2 eps_i) (Eq.
  * disp-pair-pot-multilevel-LorentzBerthelot, seven instances of the
  * method), and the interpolation pairs channel k with 6-k.
- *   pos      device, N x 3 (plan precision), any positions
- *   sigma    device, N (plan precision), > 0
- *   epsilon  device, N (plan precision), >= 0
+ *   pos      N x 3 (plan precision), any positions
+ *   sigma    N (plan precision), > 0
+ *   epsilon  N (plan precision), >= 0
+ *            (these three: device or page-locked host memory, as for
+ *            mls6_eval's pos; other host memory returns MLS6_ERR_ARG)
  *   forces   device, N x 3, overwritten
  *   energy   host or device double, or NULL
  * No virial.  Kernels are launched one by one (no graph) on the plan's

@@ -55,6 +55,20 @@ static bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Positions and coefficients are read only by the binning kernels: device
+// memory, or page-locked host memory that the device addresses through the
+// same pointer (unified addressing; the kernel then reads it over the host
+// link).  Anything else is refused rather than handed to a kernel.
+static bool device_readable(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeHost && at.devicePointer == ptr;
+}
+
 static int dev_of(const Plan*) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -284,6 +298,7 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
   const T* cc = (const T*)c_;
   T* forces = (T*)forces_;
   if (N > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+  if (N > 0 && (!device_readable(pos) || (cc && !device_readable(cc)))) return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;
   double* energy_dev = (energy && is_device_ptr(energy)) ? energy : nullptr;
@@ -359,6 +374,8 @@ static int eval_lb_t(Plan* p, const T* pos, const T* sigma, const T* eps, T* for
     return MLS6_OK;
   }
   if (!pos || !sigma || !eps || !forces) return MLS6_ERR_ARG;
+  if (!device_readable(pos) || !device_readable(sigma) || !device_readable(eps))
+    return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;
   const long np1 = p->lv[1].np;
