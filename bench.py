@@ -66,7 +66,7 @@ TRAFFIC = {
 
 # arithmetic of each precision mode (pair/grid transfers; level stencils)
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16x3"}
-DEFAULT_PREC = {"cube1m": "mixed"}
+DEFAULT_PREC = {"cube1m": "mixed", "slab4m": "fp32"}
 
 
 def parse():
@@ -334,12 +334,13 @@ def oracle_full(O, w, xd, cd):
     return time.perf_counter() - t0
 
 
-def oracle_single_thread(O, w, xd, cd, frac=16):
+def oracle_single_thread(O, w, xd, cd, frac=0):
     """Single-thread oracle time of a full evaluation from a bounded sample:
     the whole grid part once and the local part of 1/frac of the atoms."""
     import numpy as np
 
     n = O.grid_dims(w.box, w.h, w.levels)
+    frac = frac or max(16, w.N // 65536)  # the local part of about 65,536 atoms
     O.set_threads(1)
     try:
         t0 = time.perf_counter()
@@ -657,11 +658,14 @@ def form_point(torch, mls6, dev, stream, flush, w, x, c, prec, a, h, levels, idx
         b.close()
 
 
-def learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, steps, log):
+def learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, steps, log,
+                  slabs=False):
     """The learned correction at cutoff a: coarse evaluation (h = 2) plus the
-    network, trained on two 32,768-atom cubes of the same density against
-    the fine (h = 1) evaluation; eps_F, throughput, and the measured floor
-    (network time per atom against the grid time the coarse grid saves)."""
+    network, trained on two 32,768-atom systems against the fine (h = 1)
+    evaluation -- cubes of the workload's density, or (slabs) slabs with the
+    proportions of the 4,194,304-atom slab; eps_F, throughput, and the
+    measured floor (network time per atom against the grid time the coarse
+    grid saves)."""
     from paper_1308_4005_gb300 import inputs as I
     from paper_1308_4005_gb300 import learn
 
@@ -670,6 +674,9 @@ def learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, steps, 
     rho = w.N / (w.box[0] * w.box[1] * w.box[2])
     train = []
     for s in range(2):
+        if slabs:
+            train.append(learn.slab_system(32768, 9300 + s))
+            continue
         tw = I.scaled_cube(32768, rho, a, 1.0, 0, 9300 + s)
         tx, tc = I.generate(tw)
         train.append((tw.box, tx, tc))
@@ -962,6 +969,28 @@ def run_ours(args):
             line["lorentz_berthelot"] = {"error": repr(e)}
         log(f"Lorentz-Berthelot done at {time.time() - t_start:.0f} s")
         line["at_1e-4"] = at
+    if rank == 0 and world == 1 and not args.quick and w.name == "slab4m":
+        # the learned-correction configuration: the coarse grid of the main
+        # line (h = 2), the same plus the network (trained on 32,768-atom
+        # slabs of the same proportions), and the fine grid (h = 1) that
+        # supplies the training targets and judges the correction
+        rng = np.random.default_rng(5)
+        idx = rng.choice(N, 2048, replace=False)
+        t0 = time.time()
+        Fex = exact_forces(x, c, w.box, idx)
+        log(f"exact forces on {idx.size} sampled atoms in {time.time() - t0:.1f} s")
+        line["eps_F"] = eps_F(F_main[idx], Fex)
+        try:
+            line["learned"] = learned_point(torch, mls6, dev, stream, flush, w, x, c, w.a, idx,
+                                            Fex, 10, log, slabs=True)
+        except Exception as e:
+            line["learned"] = {"error": repr(e)}
+        log(f"learned done at {time.time() - t_start:.0f} s")
+        try:
+            line["fine_judge"] = form_point(torch, mls6, dev, stream, flush, w, x, c, "fp32",
+                                            w.a, 1.0, 0, idx, Fex, 10)
+        except Exception as e:
+            line["fine_judge"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.time()
         line["cpu_baseline"] = oracle_baseline(w, x, c)

@@ -52,6 +52,11 @@ def workload(name: str) -> Workload:
                      4 levels (top grid 4x4x12).
     ``cube1m``       N=1,048,576 uniform fluid at rho=0.85 in a periodic cube,
                      C6 in [0.5,1.5], a=3, h=1, 5 levels.
+    ``slab4m``       N=4,194,304 liquid slab at rho=0.8 in a periodic
+                     160x160x240 box, centred, N/(rho 160^2) = 204.8 thick (N and
+                     rho fixed), C6 in [0.5,1.5]; a=3 and the coarse grid of the
+                     learned correction, h=2, 5 levels (the automatic rule:
+                     80x80x128 finest grid).
     """
     if name == "cube1000":
         return Workload(name, 1000, (10.0, 10.0, 10.0), _cube(10.0), (0.5, 1.5), 2.5, 1.0, 3,
@@ -66,6 +71,12 @@ def workload(name: str) -> Workload:
         N, rho = 1 << 20, 0.85
         L = (N / rho) ** (1.0 / 3.0)
         return Workload(name, N, (L, L, L), _cube(L), (0.5, 1.5), 3.0, 1.0, 5, SEED_BASE + 2)
+    if name == "slab4m":
+        N, rho, Lx, Lz = 1 << 22, 0.8, 160.0, 240.0
+        t = N / (rho * Lx * Lx)
+        z0 = 0.5 * (Lz - t)
+        return Workload(name, N, (Lx, Lx, Lz), ((0.0, Lx), (0.0, Lx), (z0, z0 + t)), (0.5, 1.5),
+                        3.0, 2.0, 5, SEED_BASE + 4)
     raise KeyError(name)
 
 
