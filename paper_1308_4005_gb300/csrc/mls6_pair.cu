@@ -1007,8 +1007,8 @@ long pair_blocks(const Plan* p, int split) {
 // 48 resident warps per SM on a 152-SM GPU.
 #ifndef MLS6_DEVICE_ONLY  // host code, left out where another unit includes this file
 int pair_split(const Plan* p) {
-  // the cluster form is not a default: on the 1M-atom cube it took 1.22 ms
-  // against 0.87 ms for the per-atom kernel (every atom of a segment is
+  // the cluster form is not a default: on the 1M-atom cube it takes 1.22 ms
+  // against 0.757 ms for the per-atom kernel (every atom of a segment is
   // evaluated against the union of the segment's candidate cells, which the
   // full lanes do not make up for)
   return pair_split_atom(p);
@@ -1017,8 +1017,8 @@ int pair_split(const Plan* p) {
 int pair_split_atom(const Plan* p) {
   // FP64: the queue form with two atoms per warp where the cell geometry
   // allows it (1M-atom cube 24.5 ms against 29.4 ms per atom and 31.2 ms
-  // for the warp form); FP32 keeps the per-atom kernel (868 us there against
-  // 2.25 ms for the best queue form)
+  // for the warp form); FP32 keeps the per-atom kernel (0.757 ms there
+  // against 2.23 ms for the best queue form)
   if (p->prec == MLS6_FP64 && pair_cluster_ok(p)) return 128;
   const long want = 152L * 48 * 32;
   int s = 1;
