@@ -59,3 +59,20 @@ def test_equal_accuracy_takes_the_fastest_spacing():
     r = bench.best_at_target(fine + far, 1e-4)
     assert r["h"] == 1.0 and r["how"] == "interpolated"
     assert bench.best_at_target([], 1e-4)["value"] is None
+
+
+def test_learned_configuration_workload():
+    """slab4m: 4,194,304 atoms at density 0.8 in a centred slab of the
+    160 x 160 x 240 box (thickness N / (0.8 * 160^2)), the coarse grid h = 2
+    with the level count of the automatic rule."""
+    from paper_1308_4005_gb300 import mls6
+
+    w = I.workload("slab4m")
+    assert w.N == 4194304 and w.box == (160.0, 160.0, 240.0)
+    (x0, x1), (y0, y1), (z0, z1) = w.region
+    t = z1 - z0
+    assert (x1 - x0, y1 - y0) == (160.0, 160.0)
+    assert w.N / (160.0 * 160.0 * t) == pytest.approx(0.8)
+    assert z0 == pytest.approx(240.0 - z1)
+    assert (w.a, w.h) == (3.0, 2.0)
+    assert w.levels == mls6.mls6_auto_levels(w.box, w.h)
