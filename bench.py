@@ -563,13 +563,15 @@ def timed_steps(torch, stream, step, steps, flush, world=1):
 class Bench:
     """Device buffers and one plan of a workload."""
 
-    def __init__(self, torch, mls6, dev, stream, box, N, a, h, levels, prec, x, c, vir=True):
+    def __init__(self, torch, mls6, dev, stream, box, N, a, h, levels, prec, x, c, vir=True,
+                 order=3):
         import numpy as np
 
         self.torch, self.mls6, self.stream = torch, mls6, stream
         dt = torch.float64 if prec == "fp64" else torch.float32
         self.N, self.prec = N, prec
-        self.plan = mls6.Plan(box, N, a, h, levels, precision=prec, stream=stream.cuda_stream)
+        self.plan = mls6.Plan(box, N, a, h, levels, precision=prec, order=order,
+                              stream=stream.cuda_stream)
         self.info = self.plan.info()
         self.pos_h = torch.tensor(np.c_[x, c], dtype=dt).pin_memory()
         self.pos = torch.empty((N, 4), dtype=dt, device=dev)
@@ -645,15 +647,16 @@ class Bench:
         self.plan.close()
 
 
-def form_point(torch, mls6, dev, stream, flush, w, x, c, prec, a, h, levels, idx, Fex, steps):
-    """Throughput and eps_F of one form at one (a, h)."""
-    b = Bench(torch, mls6, dev, stream, w.box, w.N, a, h, levels, prec, x, c)
+def form_point(torch, mls6, dev, stream, flush, w, x, c, prec, a, h, levels, idx, Fex, steps,
+               order=3):
+    """Throughput and eps_F of one form at one (a, h, interpolation order)."""
+    b = Bench(torch, mls6, dev, stream, w.box, w.N, a, h, levels, prec, x, c, order=order)
     try:
         b.warm(3)
         ms = statistics.mean(timed_steps(torch, stream, b.step, steps, flush))
         e = eps_F(b.forces()[idx], Fex)
-        return {"a": a, "h": h, "levels": b.info["levels"], "ms": ms, "value": w.N / (ms / 1e3),
-                "eps_F": e, "stencil_kind": b.info["stencil_kind"]}
+        return {"a": a, "h": h, "order": order, "levels": b.info["levels"], "ms": ms,
+                "value": w.N / (ms / 1e3), "eps_F": e, "stencil_kind": b.info["stencil_kind"]}
     finally:
         b.close()
 
@@ -932,13 +935,26 @@ def run_ours(args):
                                                       prec, a, h, lev, idx, Fex, 10))
                     except Exception as e:  # report, keep the main line
                         sweep[prec].append({"a": a, "h": h, "error": repr(e)})
+        # the quintic basis (order 5, Sec. III.B's comparison): smaller
+        # interpolation error at a given h/a for 216 instead of 64 nodes per atom
+        sweep["fp32_order5"] = []
+        for h in (1.5 * w.h, 2.0 * w.h):
+            for a in (2.5, 3.0, 3.5):
+                try:
+                    sweep["fp32_order5"].append(form_point(torch, mls6, dev, stream, flush, w, x,
+                                                           c, "fp32", a, h, 0, idx, Fex, 10,
+                                                           order=5))
+                except Exception as e:
+                    sweep["fp32_order5"].append({"a": a, "h": h, "order": 5, "error": repr(e)})
         log(f"sweep done at {time.time() - t_start:.0f} s")
-        line["forms"] = {p: dict(v[0]) for p, v in sweep.items() if v and "value" in v[0]}
+        line["forms"] = {p: dict(v[0]) for p, v in sweep.items()
+                         if p in ("fp32", "mixed") and v and "value" in v[0]}
         line["sweep"] = sweep
         # best over h, and along the workload's own h
         at = {p: dict(best_at_target(v),
                       at_workload_h=at_target([q for q in v if q.get("h") == w.h]))
-              for p, v in sweep.items()}
+              for p, v in sweep.items() if p in ("fp32", "mixed")}
+        at["fp32_order5"] = best_at_target(sweep["fp32_order5"])
         try:
             lp = [learned_point(torch, mls6, dev, stream, flush, w, x, c, a, idx, Fex, 10, log)
                   for a in (3.0, 3.5)]
