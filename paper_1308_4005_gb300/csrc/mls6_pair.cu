@@ -159,11 +159,11 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
               }
               e += cj * g0;
               const T cg = cj * gp;
-              const T cgx = cg * ddx, cgy = cg * ddy, cgz = cg * ddz;
-              fx += cgx;
-              fy += cgy;
-              fz += cgz;
-              if (VIR && shifted) {
+              fx += cg * ddx;
+              fy += cg * ddy;
+              fz += cg * ddz;
+              if (VIR && shifted) {  // runs across a periodic face only
+                const T cgx = cg * ddx, cgy = cg * ddy, cgz = cg * ddz;
                 sfx += cgx;
                 sfy += cgy;
                 sfz += cgz;
