@@ -147,7 +147,11 @@ template <typename T> static int upload_tables_t(Plan* p) {
   p->n_epart = std::max(1L, cdiv(N, kBlock));
   // room for the largest lane split, so that the split can be retuned
   // without reallocation; records a smaller split does not write stay zero
-  p->n_pair_blocks = std::max(1L, cdiv(N * kPairSplitMax, kBlock));
+  // virial partials of the pair sum: one per warp of the per-atom kernel
+  // (<= 8 lanes per atom; every warp of its blocks, up to kBlock-thread
+  // blocks, writes one), one per block of the other forms
+  p->n_pair_blocks =
+      std::max(1L, std::max(cdiv(N * 8, (long)kBlock) * (kBlock / 32), cdiv(N * kPairSplitMax, kBlock)));
   p->wpart_stencil = 0;
   p->wpart_top = p->stencil_blocks;
   p->wpart_pair = p->wpart_top + np_top;

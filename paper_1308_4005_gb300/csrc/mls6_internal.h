@@ -28,6 +28,7 @@ constexpr int kStencilW = 4;      // consecutive x outputs per stencil thread
 constexpr size_t kStencilSmemMax = 200 * 1024;  // dynamic shared memory of a stencil tile
 constexpr double kCellDiv = 2.0;  // cell width >= a / kCellDiv
 constexpr int kPairCluster = 1024;  // pair_split code of the cluster form
+constexpr int kPairAtomBlock = 64;  // threads per block of the one-lane-per-atom pair kernel
 constexpr int kPairSplitMax = 32;  // pair-kernel blocks are at most N * kPairSplitMax / kBlock
 
 __host__ __device__ inline long cdiv(long a, long b) { return (a + b - 1) / b; }

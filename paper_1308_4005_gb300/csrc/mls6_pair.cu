@@ -93,7 +93,6 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
                                                   T* __restrict__ floc,
                                                   double* __restrict__ wpart,
                                                   const T* __restrict__ lbw) {
-  __shared__ double sh[32 * 6];
   const int gid = bk.x * blockDim.x + threadIdx.x;
   const int i = gid / S, sub = gid % S;
   T e = 0, fx = 0, fy = 0, fz = 0;
@@ -209,10 +208,17 @@ __device__ __forceinline__ void k_pair_body(const Blk bk,const Vec4<T>* __restri
     floc[3 * (size_t)i + 2] = -cf * fz;
   }
   if (VIR) {
-    double ws[6];
-    block_sum_lo<T, 6>(wv, ws, sh);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) wpart[6 * (size_t)bk.x + c] = 0.5 * ws[c];
+    // one partial per warp, at its global warp index: the partials, and so
+    // the virial, do not depend on the block size the body runs with (a
+    // single plan's launch or the persistent kernel of a batch)
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      for (int o = 16; o > 0; o >>= 1) wv[c] += __shfl_down_sync(0xffffffffu, wv[c], o);
+    if ((threadIdx.x & 31) == 0) {
+      const size_t wg = ((size_t)bk.x * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) wpart[6 * wg + c] = 0.5 * (double)wv[c];
+    }
   }
 }
 
@@ -998,7 +1004,8 @@ long pair_blocks(const Plan* p, int split) {
   if (N <= 0) return 0;
   if (split == kPairCluster) return cdiv(N, (long)kBlock / 4);  // 8 atoms per warp
   if (split >= 64) return cdiv(cdiv(N, split / 64), kQWarps);
-  return cdiv(N * split, kBlock);
+  if (split <= 8) return cdiv(N * split, 32L);  // per-atom kernel: one virial partial per warp
+  return cdiv(N * split, kBlock);                // warp form: one per block
 }
 #endif  // MLS6_DEVICE_ONLY
 
@@ -1027,31 +1034,37 @@ int pair_split_atom(const Plan* p) {
 }
 #endif  // MLS6_DEVICE_ONLY
 
+// One lane per atom runs in small blocks (kPairAtomBlock): the block's
+// warps end at different times (their atoms' candidate counts differ), and a
+// small block gives its SM slot back sooner, to the next pair block or to the
+// grid chain running beside the pair sum (1M-atom cube: step 1.230 ->
+// 1.214 ms against 256-thread blocks, 1.222 ms with 128).
 template <typename T, int S>
 static void launch_s(Plan* p, const PairArgs<T>& pg, bool vir, bool lb, cudaStream_t st) {
   const int N = (int)p->N;
-  const long nb = cdiv((long)N * S, kBlock);
+  const int TB = S == 1 ? kPairAtomBlock : kBlock;
+  const long nb = cdiv((long)N * S, TB);
   if (p->sm.n != 2 && !lb) {  // smoothing function other than Eq. (gamma)
     if (vir)
-      k_pair<T, true, S, false, true><<<nb, kBlock, 0, st>>>(
+      k_pair<T, true, S, false, true><<<nb, TB, 0, st>>>(
           (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
           p->d_wpart + 6 * p->wpart_pair);
     else
-      k_pair<T, false, S, false, true><<<nb, kBlock, 0, st>>>(
+      k_pair<T, false, S, false, true><<<nb, TB, 0, st>>>(
           (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
           p->d_wpart + 6 * p->wpart_pair);
     return;
   }
   if (lb)
-    k_pair<T, false, S, true><<<nb, kBlock, 0, st>>>(
+    k_pair<T, false, S, true><<<nb, TB, 0, st>>>(
         (const Vec4<T>*)p->d_sorted, p->d_cell_start, N, pg, (T*)p->d_e0, (T*)p->d_floc,
         p->d_wpart + 6 * p->wpart_pair, (const T*)p->d_lbw);
   else if (vir)
-    k_pair<T, true, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+    k_pair<T, true, S><<<nb, TB, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
                                               pg, (T*)p->d_e0, (T*)p->d_floc,
                                               p->d_wpart + 6 * p->wpart_pair);
   else
-    k_pair<T, false, S><<<nb, kBlock, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
+    k_pair<T, false, S><<<nb, TB, 0, st>>>((const Vec4<T>*)p->d_sorted, p->d_cell_start, N,
                                                pg, (T*)p->d_e0, (T*)p->d_floc,
                                                p->d_wpart + 6 * p->wpart_pair);
 }
