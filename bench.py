@@ -56,7 +56,6 @@ EXACT_R = 20.0          # radius of the direct sums behind the exact sampled for
 # capture has no entry and reports null.
 TRAFFIC = {
     ("cube1m", "mixed", "bin"): 84425728,          # k_bin, scans, k_scatter, k_cellsort
-    ("cube1m", "mixed", "pair"): 18244096,         # k_pair<float, 1>: sorted atoms + cell starts
     ("cube1m", "mixed", "anterpolate"): 28061184,  # k_anterp + k_from_fixed
     ("cube1m", "mixed", "restrict"): 6534656,      # k_restrict, 4 levels
     ("cube1m", "mixed", "stencil"): 8270080,       # k_stencil_mma<1>: q of levels 1-4
