@@ -988,7 +988,7 @@ def run_ours(args):
         # the learned-correction configuration: the coarse grid of the main
         # line (h = 2), the same plus the network (trained on 32,768-atom
         # slabs of the same proportions), and the fine grid (h = 1) that
-        # supplies the training targets and judges the correction
+        # supplies the training targets and the accuracy check of the correction
         rng = np.random.default_rng(5)
         idx = rng.choice(N, 2048, replace=False)
         t0 = time.time()
@@ -1002,10 +1002,10 @@ def run_ours(args):
             line["learned"] = {"error": repr(e)}
         log(f"learned done at {time.time() - t_start:.0f} s")
         try:
-            line["fine_judge"] = form_point(torch, mls6, dev, stream, flush, w, x, c, "fp32",
+            line["fine_grid"] = form_point(torch, mls6, dev, stream, flush, w, x, c, "fp32",
                                             w.a, 1.0, 0, idx, Fex, 10)
         except Exception as e:
-            line["fine_judge"] = {"error": repr(e)}
+            line["fine_grid"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.time()
         line["cpu_baseline"] = oracle_baseline(w, x, c)
