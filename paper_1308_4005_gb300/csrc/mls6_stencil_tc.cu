@@ -41,7 +41,7 @@ constexpr int kTcX = 16, kTcY = 16, kTcZ = 8;
 // A fragments of a tap row serve 4 line groups; measured on the 1M-atom
 // cube: 180 vs 238 us without the virial, 422 vs 439 us with it
 template <bool VIR> __host__ __device__ constexpr int tc_warps() { return VIR ? 4 : 8; }
-constexpr int kTcWin = 32;                            // x window
+// the x window of a tile is 32 nodes (16 outputs and the stencil's halo)
 constexpr int kTcPitch = 40;                          // bf16 per staged line (80 B)
 constexpr int kTcWords = 64;                          // packed pairs per row, part, channel
 
