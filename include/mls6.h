@@ -73,7 +73,9 @@ typedef enum {
 } mls6_precision;
 
 /* Finest-grid size for a box (per axis the multiple of 2^(levels-1) nearest
- * to L/h, ties to the finer grid).  Host only; needs no GPU.
+ * to L/h, ties to the finer grid: every coarser level then halves the node
+ * count, Sec. II.A.4, and the rule gives the 12 x 12 x 192 grid of the slab
+ * example in Sec. III.C).  Host only; needs no GPU.
  * box: 3 doubles (Lx, Ly, Lz).  n_out: 3 ints.  Returns MLS6_OK or an error
  * (MLS6_ERR_SIZE for a finest grid of more than 2^31 - 1 nodes, which the
  * grid kernels cannot index; mls6_plan returns the same). */
@@ -192,8 +194,10 @@ int mls6_eval(mls6_plan_t* p, const void* pos, const void* c, void* forces, doub
               double* virial);
 
 /* As mls6_eval, and also writes the per-atom energies
- * -1/2 c_i (e0_i + e_i) + 1/2 (gamma(0)/a^6) c_i^2 (they sum to E) to the
- * device array atom_energy (N doubles). */
+ * -1/2 c_i (e0_i + e_i) + 1/2 (gamma(0)/a^6) c_i^2 (they sum to E; the
+ * terms of Eq. pot-initial-splitting taken atom by atom, the last one the
+ * self term of Eq. self-interaction-energy) to the device array atom_energy
+ * (N doubles). */
 int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces, double* energy,
                     double* virial, double* atom_energy);
 
