@@ -35,7 +35,8 @@ def test_job_throughput_uses_slowest_rank():
     import torch.multiprocessing as mp
 
     world, port = 2, _free_port()
-    mgr = mp.Manager()
+    # the manager's server process is spawned too: no fork of a threaded process
+    mgr = mp.get_context("spawn").Manager()
     results = mgr.dict()
     mp.spawn(_worker, args=(world, port, results), nprocs=world, join=True)
     for r in range(world):
