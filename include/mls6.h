@@ -182,7 +182,9 @@ int mls6_set_graph(mls6_plan_t* p, int enable);
  *   c       N coefficients c_i = sqrt(C6_i) (plan precision), device or
  *           page-locked host memory as pos, or NULL (coefficients in the 4th
  *           column of pos).
- *   forces  device pointer, N x 3 of the plan precision, overwritten.
+ *   forces  device pointer, N x 3 of the plan precision, overwritten
+ *           (page-locked host memory also works; other host memory returns
+ *           MLS6_ERR_ARG).
  *   energy  one double, host or device pointer, or NULL to skip.
  *   virial  six doubles (xx yy zz xy xz yz), host or device, or NULL to skip
  *           (skipping it also skips the virial arithmetic).
@@ -197,7 +199,7 @@ int mls6_eval(mls6_plan_t* p, const void* pos, const void* c, void* forces, doub
  * -1/2 c_i (e0_i + e_i) + 1/2 (gamma(0)/a^6) c_i^2 (they sum to E; the
  * terms of Eq. pot-initial-splitting taken atom by atom, the last one the
  * self term of Eq. self-interaction-energy) to the device array atom_energy
- * (N doubles). */
+ * (N doubles; other host memory than page-locked returns MLS6_ERR_ARG). */
 int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces, double* energy,
                     double* virial, double* atom_energy);
 
@@ -214,7 +216,8 @@ int mls6_eval_atoms(mls6_plan_t* p, const void* pos, const void* c, void* forces
  *   epsilon  N (plan precision), >= 0
  *            (these three: device or page-locked host memory, as for
  *            mls6_eval's pos; other host memory returns MLS6_ERR_ARG)
- *   forces   device, N x 3, overwritten
+ *   forces   device, N x 3, overwritten (as mls6_eval: MLS6_ERR_ARG for
+ *            host memory that is not page-locked)
  *   energy   host or device double, or NULL
  * No virial.  Kernels are launched one by one (no graph) on the plan's
  * stream; a host energy makes the call wait and report MLS6_ERR_NONFINITE.

@@ -58,7 +58,9 @@ static bool is_device_ptr(const void* ptr) {
 // Positions and coefficients are read only by the binning kernels: device
 // memory, or page-locked host memory that the device addresses through the
 // same pointer (unified addressing; the kernel then reads it over the host
-// link).  Anything else is refused rather than handed to a kernel.
+// link).  The same test guards the per-atom outputs (forces, per-atom
+// energies), which kernels write.  Anything else is refused rather than
+// handed to a kernel.
 static bool device_readable(const void* ptr) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -302,7 +304,9 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
   const T* cc = (const T*)c_;
   T* forces = (T*)forces_;
   if (N > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
-  if (N > 0 && (!device_readable(pos) || (cc && !device_readable(cc)))) return MLS6_ERR_ARG;
+  if (N > 0 && (!device_readable(pos) || (cc && !device_readable(cc)) || !device_readable(forces) ||
+                (atom_energy && !device_readable(atom_energy))))
+    return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;
   double* energy_dev = (energy && is_device_ptr(energy)) ? energy : nullptr;
@@ -378,7 +382,8 @@ static int eval_lb_t(Plan* p, const T* pos, const T* sigma, const T* eps, T* for
     return MLS6_OK;
   }
   if (!pos || !sigma || !eps || !forces) return MLS6_ERR_ARG;
-  if (!device_readable(pos) || !device_readable(sigma) || !device_readable(eps))
+  if (!device_readable(pos) || !device_readable(sigma) || !device_readable(eps) ||
+      !device_readable(forces))
     return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;
