@@ -345,7 +345,9 @@ int mls6_batch_set_stream(mls6_batch_t* b, void* stream);
 
 /* Evaluate all replicas.  pos, c, forces: device arrays concatenating the
  * replicas in order (replica r starts at atom offsets[r] of
- * mls6_batch_size), laid out as for mls6_eval.  energy: B doubles, virial:
+ * mls6_batch_size), laid out as for mls6_eval (page-locked host memory also
+ * works; other host memory returns MLS6_ERR_ARG, here and in
+ * mls6_batch_tune).  energy: B doubles, virial:
  * 6B doubles (NULL skips the virial), host or device; host pointers make the
  * call wait and report MLS6_ERR_NONFINITE if any replica saw a non-finite
  * input.  The first call with a set of pointers captures the graph. */

@@ -268,6 +268,24 @@ static bool is_dev(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Arrays the kernels read or write: device memory, or page-locked host
+// memory that the device addresses through the same pointer.  Other host
+// memory is refused before anything is captured or launched.
+static bool kernel_addressable(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeHost && at.devicePointer == ptr;
+}
+
+static bool arrays_ok(const void* pos, const void* c, const void* forces) {
+  return pos && forces && kernel_addressable(pos) && kernel_addressable(forces) &&
+         (!c || kernel_addressable(c));
+}
+
 static int launch(Batch* b, const void* pos, const void* c, void* forces, bool vir) {
   Batch::Key key = {pos, c, forces, vir};
   if (!b->gexec || !(key == b->key)) {
@@ -283,7 +301,7 @@ static int launch(Batch* b, const void* pos, const void* c, void* forces, bool v
 static int eval(Batch* b, const void* pos, const void* c, void* forces, double* energy,
                 double* virial) {
   const int64_t ntot = b->off[b->B];
-  if (ntot > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+  if (ntot > 0 && !arrays_ok(pos, c, forces)) return MLS6_ERR_ARG;
   const bool vir = virial != nullptr;
   int rc = launch(b, pos, c, forces, vir);
   if (rc) return rc;
@@ -571,7 +589,7 @@ int mls6_batch_tune(mls6_batch_t* batch, const void* pos, const void* c, void* f
                     double* best_sec) {
   if (!batch || reps < 1) return MLS6_ERR_ARG;
   Batch* b = reinterpret_cast<Batch*>(batch);
-  if (b->off[b->B] > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
+  if (b->off[b->B] > 0 && !arrays_ok(pos, c, forces)) return MLS6_ERR_ARG;
   double t0 = 0.0;
   int rc = tune_form(b, pos, c, forces, reps, &t0);
   if (rc) return rc;
