@@ -445,6 +445,8 @@ void mls6_batch_destroy(mls6_batch_t* b);
  * and H^T dZ, bias gradients as products with a ones operand), partial sums
  * over blocks of atoms reduced in a fixed order (reproducible bit for bit);
  * Adam (0.9, 0.999, 1e-8) on FP32 master weights.
+ * Arrays described as device may also be page-locked host memory; other
+ * host memory returns MLS6_ERR_ARG.
  * All calls are asynchronous on the model's stream (mls6_mlp_set_stream)
  * except where a host result is returned; calls that take a plan run on the
  * plan's stream.
@@ -508,14 +510,14 @@ void mls6_mlp_destroy(mls6_mlp_t* m);
  *   virial  device, 6 doubles, written (or NULL):
  *           1/2 sum_mu q_mu sum_nu V_c[(mu-nu) mod n] q_nu
  *   stream  cudaStream_t (NULL = legacy default stream); asynchronous.
+ * q, T, V, e and virial may also be page-locked host memory; other host
+ * memory returns MLS6_ERR_ARG (checked after the grid size).
  * Its scratch (six doubles per node) is one fixed file-scope device array of
  * 192 KiB that every GPU loading the library holds until the process exits.
- * The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress) and keeps it for the life of the process; make
- * that first call before any stream capture.  A cudaDeviceReset (or
- * anything else that destroys the device's primary context) invalidates
- * the kept address: do not call this entry point on that device again in
- * the same process.
+ * Every call looks up that array's device address in the current context
+ * (cudaGetSymbolAddress), so a cudaDeviceReset leaves nothing stale.  The
+ * first call on a device may load the library's kernels, so make it before
+ * any stream capture.
  * All calls share the array and every entry a call reads is written by the
  * same call, so nothing needs clearing, but calls that overlap on the GPU
  * (different streams, or different host threads) race on it. */

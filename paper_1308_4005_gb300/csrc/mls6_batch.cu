@@ -268,19 +268,6 @@ static bool is_dev(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Arrays the kernels read or write: device memory, or page-locked host
-// memory that the device addresses through the same pointer.  Other host
-// memory is refused before anything is captured or launched.
-static bool kernel_addressable(const void* ptr) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
-  return at.type == cudaMemoryTypeHost && at.devicePointer == ptr;
-}
-
 static bool arrays_ok(const void* pos, const void* c, const void* forces) {
   return pos && forces && kernel_addressable(pos) && kernel_addressable(forces) &&
          (!c || kernel_addressable(c));

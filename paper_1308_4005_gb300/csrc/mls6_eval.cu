@@ -55,22 +55,6 @@ static bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Positions and coefficients are read only by the binning kernels: device
-// memory, or page-locked host memory that the device addresses through the
-// same pointer (unified addressing; the kernel then reads it over the host
-// link).  The same test guards the per-atom outputs (forces, per-atom
-// energies), which kernels write.  Anything else is refused rather than
-// handed to a kernel.
-static bool device_readable(const void* ptr) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
-  return at.type == cudaMemoryTypeHost && at.devicePointer == ptr;
-}
-
 static int dev_of(const Plan*) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -304,8 +288,10 @@ static int eval_t(Plan* p, const void* pos_, const void* c_, void* forces_, doub
   const T* cc = (const T*)c_;
   T* forces = (T*)forces_;
   if (N > 0 && (!pos || !forces)) return MLS6_ERR_ARG;
-  if (N > 0 && (!device_readable(pos) || (cc && !device_readable(cc)) || !device_readable(forces) ||
-                (atom_energy && !device_readable(atom_energy))))
+  // inputs and per-atom outputs: device or page-locked host memory only
+  if (N > 0 && (!kernel_addressable(pos) || (cc && !kernel_addressable(cc)) ||
+                !kernel_addressable(forces) ||
+                (atom_energy && !kernel_addressable(atom_energy))))
     return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;
@@ -382,8 +368,8 @@ static int eval_lb_t(Plan* p, const T* pos, const T* sigma, const T* eps, T* for
     return MLS6_OK;
   }
   if (!pos || !sigma || !eps || !forces) return MLS6_ERR_ARG;
-  if (!device_readable(pos) || !device_readable(sigma) || !device_readable(eps) ||
-      !device_readable(forces))
+  if (!kernel_addressable(pos) || !kernel_addressable(sigma) || !kernel_addressable(eps) ||
+      !kernel_addressable(forces))
     return MLS6_ERR_ARG;
   int rc = ensure_streams(p);
   if (rc) return rc;

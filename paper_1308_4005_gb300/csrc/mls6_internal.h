@@ -33,6 +33,21 @@ constexpr int kPairSplitMax = 32;  // pair-kernel blocks are at most N * kPairSp
 
 __host__ __device__ inline long cdiv(long a, long b) { return (a + b - 1) / b; }
 
+// A caller's array that kernels read or write: device (or managed) memory,
+// or page-locked host memory that the device addresses through the same
+// pointer (unified addressing; kernels then reach it over the host link).
+// The entry points refuse anything else with MLS6_ERR_ARG rather than hand
+// it to a kernel.  Host only.
+inline bool kernel_addressable(const void* ptr) {
+  cudaPointerAttributes at;
+  if (!ptr || cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeHost && at.devicePointer == ptr;
+}
+
 // 4-wide records: {x, y, z, c} positions, stencil tap weights.
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 {
   T x, y, z, w;

@@ -972,20 +972,23 @@ int mls6_mlp_features(mls6_plan_t* plan, const mls6_mlp_t* mm, void* out, int fm
   if (!plan || !mm || (fmt != 0 && fmt != 1)) return MLS6_ERR_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (p->order != 3) return MLS6_ERR_ORDER;  // features are defined on the cubic basis
-  if (p->N > 0 && !out) return MLS6_ERR_ARG;
+  if (p->N > 0 && !kernel_addressable(out)) return MLS6_ERR_ARG;
   Mlp* m = const_cast<Mlp*>(reinterpret_cast<const Mlp*>(mm));
   return p->prec == MLS6_FP64 ? features_t<double>(p, m, out, fmt, false, p->stream)
                               : features_t<float>(p, m, out, fmt, false, p->stream);
 }
 
 int mls6_mlp_forward(mls6_mlp_t* mm, const void* X, int64_t N, float* Y) {
-  if (!mm || N < 0 || (N > 0 && (!X || !Y))) return MLS6_ERR_ARG;
+  if (!mm || N < 0 || (N > 0 && (!kernel_addressable(X) || !kernel_addressable(Y))))
+    return MLS6_ERR_ARG;
   return forward(reinterpret_cast<Mlp*>(mm), X, N, Y, false);
 }
 
 int mls6_mlp_grad(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, float* grad,
                   double* loss) {
-  if (!mm || N < 1 || !X || !T || (reinterpret_cast<uintptr_t>(X) & 15)) return MLS6_ERR_ARG;
+  if (!mm || N < 1 || !kernel_addressable(X) || !kernel_addressable(T) ||
+      (reinterpret_cast<uintptr_t>(X) & 15))
+    return MLS6_ERR_ARG;
   Mlp* m = reinterpret_cast<Mlp*>(mm);
   int rc = gradient(m, X, T, N);
   if (rc) return rc;
@@ -997,7 +1000,8 @@ int mls6_mlp_grad(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, floa
 
 int mls6_mlp_train_step(mls6_mlp_t* mm, const void* X, const float* T, int64_t N, float lr,
                         double* loss) {
-  if (!mm || N < 1 || !X || !T || !(lr > 0.f) || (reinterpret_cast<uintptr_t>(X) & 15))
+  if (!mm || N < 1 || !kernel_addressable(X) || !kernel_addressable(T) || !(lr > 0.f) ||
+      (reinterpret_cast<uintptr_t>(X) & 15))
     return MLS6_ERR_ARG;
   Mlp* m = reinterpret_cast<Mlp*>(mm);
   int rc = gradient(m, X, T, N);
@@ -1020,7 +1024,7 @@ int mls6_mlp_apply(mls6_plan_t* plan, mls6_mlp_t* mm, void* forces) {
   if (p->order != 3) return MLS6_ERR_ORDER;
   const long N = p->N;
   if (N == 0) return MLS6_OK;
-  if (!forces) return MLS6_ERR_ARG;
+  if (!kernel_addressable(forces)) return MLS6_ERR_ARG;
   int rc = grow(m, N);
   if (rc) return rc;
   cudaStream_t saved = m->stream;

@@ -91,6 +91,9 @@ extern "C" int mls6_coarse_apply_noalloc(const double* q, const int n[3], const 
   if (n[0] < 1 || n[1] < 1 || n[2] < 1) return MLS6_ERR_GRID;
   const long np = (long)n[0] * n[1] * n[2];
   if (np > kNoAllocMaxNodes) return MLS6_ERR_SIZE;
+  if (!kernel_addressable(q) || !kernel_addressable(T) || !kernel_addressable(e) ||
+      (virial && (!kernel_addressable(V) || !kernel_addressable(virial))))
+    return MLS6_ERR_ARG;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;
